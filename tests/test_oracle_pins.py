@@ -1,0 +1,440 @@
+"""Pins for the FP64 oracle: closed forms, invariants, brute force and special
+cases that reduce to library routines.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.ndimage
+
+import oracle as O
+from paper_2103_10329_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def make_scan(n, nviews=12, seed=1, drift=None, nu=None, nv=None, flat_z=False):
+    th, z = synth.trajectory(nviews, seed)
+    nu = nu or int(round(1.5 * n))
+    nv = nv or nu
+    if flat_z:
+        z = np.zeros_like(z)
+    return O.Scan(n=n, nu=nu, nv=nv, theta=th, z=z, pitch=synth.default_pitch(nu), drift=drift)
+
+
+# ---------------------------------------------------------------- geometry
+
+def test_geometry_conventions():
+    """Sec. 2: distances are measured from the source; the detector is flat and
+    faces the source; its pixel grid is centred on the source-axis line."""
+    scan = make_scan(16, nviews=7)
+    g = O.level_geometry(scan, 0)
+    for k in range(g.n_views):
+        s = g.src[k]
+        assert math.isclose(math.hypot(s[0], s[1]), 2.0, rel_tol=1e-14)
+        assert math.isclose(s[2], scan.z[k], abs_tol=1e-15)
+        centre = g.det[k] + 0.5 * (g.nu - 1) * g.pu[k] + 0.5 * (g.nv - 1) * g.pv[k]
+        v = centre - s
+        assert math.isclose(np.linalg.norm(v), 4.0, rel_tol=1e-14)
+        # the detector centre lies on the line from the source through the rotation axis
+        assert abs(v[2]) < 1e-14 and abs(s[0] * v[1] - s[1] * v[0]) < 1e-12
+        assert s[0] * v[0] + s[1] * v[1] < 0
+        # pixel steps orthogonal to each other and to the viewing direction
+        assert abs(np.dot(g.pu[k], g.pv[k])) < 1e-15
+        assert abs(np.dot(g.pu[k], v)) < 1e-13 and abs(np.dot(g.pv[k], v)) < 1e-13
+        assert math.isclose(np.linalg.norm(g.pu[k]), scan.pitch, rel_tol=1e-14)
+
+
+def test_geometry_drift_moves_source_and_detector():
+    drift = np.zeros((5, 5))
+    drift[:, 0] = 1.0   # source +1 pixel along u
+    drift[:, 3] = -2.0  # detector -2 pixels along v
+    drift[:, 4] = 0.1   # tilt
+    scan0 = make_scan(16, nviews=5)
+    scan1 = make_scan(16, nviews=5, drift=drift)
+    g0, g1 = O.level_geometry(scan0, 0), O.level_geometry(scan1, 0)
+    eu = g0.pu / scan0.pitch
+    ev = g0.pv / scan0.pitch
+    np.testing.assert_allclose(g1.src - g0.src, eu * scan0.pitch, atol=1e-15)
+    c0 = g0.det + 0.5 * (g0.nu - 1) * g0.pu + 0.5 * (g0.nv - 1) * g0.pv
+    c1 = g1.det + 0.5 * (g1.nu - 1) * g1.pu + 0.5 * (g1.nv - 1) * g1.pv
+    np.testing.assert_allclose(c1 - c0, -2.0 * ev * scan0.pitch, atol=1e-14)
+    cosang = np.sum(g1.pu * g0.pu, axis=1) / scan0.pitch ** 2
+    np.testing.assert_allclose(cosang, math.cos(0.1), rtol=1e-14)
+
+
+def test_coarse_grid_pixels_are_fine_pixel_means():
+    """Restricted data (2x2 mean) sits at the centre of its four fine pixels."""
+    scan = make_scan(16, nviews=3)
+    g0, g1 = O.level_geometry(scan, 0), O.level_geometry(scan, 1)
+    for k in range(3):
+        p0 = O.pixel_centres(g0, k)
+        p1 = O.pixel_centres(g1, k)
+        mean = p0.reshape(g1.nv, 2, g1.nu, 2, 3).mean(axis=(1, 3))
+        np.testing.assert_allclose(p1, mean, atol=1e-14)
+
+
+# ---------------------------------------------------------------- P (= A)
+
+def test_blob_integrals_second_order():
+    """Gaussian blob: closed-form line integral amp sigma sqrt(2 pi) exp(-d^2/2s^2).
+    Joseph's bilinear sampling is second order: the error falls ~4x per
+    doubling of N once sigma >= 3h."""
+    th, z = synth.trajectory(10, 3)
+    drift = synth.drift_walk(10, 4, sigma_px=0.5, half_diag_px=20)
+    ph = synth.blobs(3, 5, 0.07, 0.1, centre_r=0.12)
+    errs = []
+    for n in (32, 64, 128):
+        nu = int(1.5 * n)
+        scan = O.Scan(n=n, nu=nu, nv=nu, theta=th, z=0.2 * z, pitch=synth.default_pitch(nu),
+                      drift=drift)
+        g = O.level_geometry(scan, 0)
+        vol = synth.voxelize_blobs(ph, n).numpy()
+        a = O.project(g, vol)
+        ex = O.blob_line_integrals(g, ph)
+        errs.append(np.abs(a - ex).max() / np.abs(ex).max())
+    assert errs[-1] < 2e-3
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+def test_ellipsoid_chords_converge():
+    """Analytic ellipsoid chords vs P of the supersampled voxelisation: the
+    mean error falls under refinement (edges make it first order)."""
+    th, z = synth.trajectory(6, 7)
+    ph = synth.ellipsoids(4, 8, axis_lo=0.08, axis_hi=0.2)
+    errs = []
+    for n in (16, 32, 64):
+        nu = int(1.5 * n)
+        scan = O.Scan(n=n, nu=nu, nv=nu, theta=th, z=0.5 * z, pitch=synth.default_pitch(nu))
+        g = O.level_geometry(scan, 0)
+        vol = synth.voxelize_ellipsoids(ph, n, supersample=4).numpy()
+        a = O.project(g, vol)
+        ex = O.ellipsoid_line_integrals(g, ph)
+        errs.append(np.abs(a - ex).mean() / np.abs(ex).mean())
+    # at least first-order convergence (edges), measured ~2.5x per doubling
+    assert errs[0] / errs[1] > 1.8 and errs[1] / errs[2] > 1.8, errs
+
+
+def _single_view(src, det, pu, pv, n, nu=1, nv=1):
+    return O.LevelGeom(n, nu, nv, 1.0 / n, np.array([src], float), np.array([det], float),
+                       np.array([pu], float), np.array([pv], float))
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_axis_aligned_ray_constant_volume(axis):
+    """A ray along a volume axis through voxel centres of a constant volume
+    samples every plane at a voxel centre: integral = N h = 1 exactly."""
+    n = 8
+    h = 1.0 / n
+    yc, zc = (2 - (n - 1) / 2) * h, (5 - (n - 1) / 2) * h
+    if axis == 0:
+        src, det = [2.0, yc, zc], [-2.0, yc, zc]
+        pu = [0.0, 0.01, 0.0]
+    else:
+        src, det = [yc, 2.0, zc], [yc, -2.0, zc]
+        pu = [0.01, 0.0, 0.0]
+    g = _single_view(src, det, pu, [0, 0, 0.01], n)
+    a = O.project(g, np.ones((n, n, n)))
+    assert a.shape == (1, 1, 1)
+    assert abs(a[0, 0, 0] - 1.0) < 1e-14
+    # and a ray through one row of voxels picks out that row only
+    vol = np.zeros((n, n, n))
+    if axis == 0:
+        vol[5, 2, :] = np.arange(n) + 1.0
+    else:
+        vol[5, :, 2] = np.arange(n) + 1.0
+    assert abs(O.project(g, vol)[0, 0, 0] - h * n * (n + 1) / 2) < 1e-13
+
+
+def test_dense_matrix_matches_entry_weights_and_transpose():
+    """Brute force at 8^3: the matrix assembled column by column from P e_j
+    equals the per-entry weight function; B e_i rows equal its transpose."""
+    n = 8
+    drift = synth.drift_walk(4, 11, sigma_px=0.7, half_diag_px=6)
+    scan = make_scan(n, nviews=4, seed=2, drift=drift, nu=12, nv=10)
+    g = O.level_geometry(scan, 0)
+    nvox = n ** 3
+    nray = g.n_views * g.nv * g.nu
+    A = np.zeros((nray, nvox))
+    for j in range(nvox):
+        e = np.zeros(nvox)
+        e[j] = 1.0
+        A[:, j] = O.project(g, e.reshape(n, n, n)).ravel()
+    W = np.zeros_like(A)
+    for k in range(g.n_views):
+        for jv in range(g.nv):
+            for ju in range(g.nu):
+                row = (k * g.nv + jv) * g.nu + ju
+                for iz in range(n):
+                    for iy in range(n):
+                        for ix in range(n):
+                            W[row, (iz * n + iy) * n + ix] = O.weight(g, k, ju, jv, ix, iy, iz)
+    assert np.count_nonzero(A) > 1000
+    np.testing.assert_allclose(A, W, rtol=0, atol=1e-14)
+    rng = np.random.default_rng(0)
+    for row in rng.choice(nray, 20, replace=False):
+        e = np.zeros(nray)
+        e[row] = 1.0
+        bt = O.backproject(g, e.reshape(g.n_views, g.nv, g.nu)).ravel()
+        np.testing.assert_allclose(bt, A[row], rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- B (= A^T)
+
+def test_adjoint_identity():
+    """Sec. 2.1: B is the adjoint of P.  <Px, y> = <x, By> to 1e-12."""
+    n = 24
+    drift = synth.drift_walk(9, 12, sigma_px=0.5, half_diag_px=18)
+    scan = make_scan(n, nviews=9, seed=3, drift=drift)
+    g = O.level_geometry(scan, 0)
+    x = synth.random_volume(n, 1)
+    y = synth.random_sino(g.n_views, g.nv, g.nu, 2)
+    lhs = float(np.vdot(O.project(g, x), y))
+    rhs = float(np.vdot(x, O.backproject(g, y)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), np.abs(x).sum())
+
+
+def test_backproject_voxels_matches_scatter():
+    n = 16
+    scan = make_scan(n, nviews=6, seed=4)
+    g = O.level_geometry(scan, 0)
+    y = synth.random_sino(g.n_views, g.nv, g.nu, 3)
+    full = O.backproject(g, y)
+    vox = synth.random_indices(40, (n, n, n), 5)
+    got = O.backproject_voxels(g, y, vox, radius=4)
+    want = full[vox[:, 2], vox[:, 1], vox[:, 0]]
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_project_rays_matches_full():
+    n = 16
+    scan = make_scan(n, nviews=5, seed=6)
+    g = O.level_geometry(scan, 0)
+    x = synth.random_volume(n, 7)
+    full = O.project(g, x)
+    rays = synth.random_indices(50, (g.n_views, g.nv, g.nu), 8)
+    got = O.project_rays(g, x, rays)
+    np.testing.assert_allclose(got, full[rays[:, 0], rays[:, 1], rays[:, 2]], rtol=1e-14)
+
+
+# ---------------------------------------------------------------- p (Eq. 5)
+
+def _golden_eq5():
+    rows = []
+    with open(os.path.join(GOLDEN, "eq5_kernel.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(t) for t in line.split()])
+    return np.array(rows).reshape(3, 3, 3) / 64.0
+
+
+def test_eq5_coefficients_and_invariants():
+    k = _golden_eq5()
+    np.testing.assert_array_equal(O.EQ5, k)
+    assert k.sum() == 0.0                       # zero DC response (Sec. 3 discussion)
+    assert abs(np.abs(k).sum() - 2.0) < 1e-15
+    assert np.array_equal(k, k[::-1, ::-1, ::-1])
+    assert np.array_equal(k, np.transpose(k, (0, 2, 1)))
+    # Fourier symbol: real, in [0, 1.625], 0 at DC, 1.625 at (pi along an in-slice axis)
+    big = np.zeros((64, 64, 64))
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                big[(dz - 1) % 64, (dy - 1) % 64, (dx - 1) % 64] = k[dz, dy, dx]
+    sym = np.fft.fftn(big)
+    assert np.abs(sym.imag).max() < 1e-13
+    assert abs(sym.real.min()) < 1e-13 and sym.real.min() > -1e-13
+    assert abs(sym.real.max() - 1.625) < 1e-13
+    assert abs(sym.real[0, 0, 32] - 1.625) < 1e-13
+
+
+@pytest.mark.parametrize("axis", [2, 0])
+def test_precondition_equals_library_correlation(axis):
+    """p * x with zero padding equals scipy's constant-mode correlation with
+    the Eq. 5 kernel (a symmetric kernel: convolution = correlation); the
+    outer index runs along the chosen slice axis."""
+    x = synth.random_volume(11, 9)
+    k = O.eq5_kernel(axis)
+    want = scipy.ndimage.correlate(x, k, mode="constant", cval=0.0)
+    np.testing.assert_allclose(O.precondition(x, axis), want, atol=1e-13)
+    # impulse response in the interior reproduces the kernel with its orientation
+    d = np.zeros((7, 7, 7))
+    d[3, 3, 3] = 1.0
+    resp = O.precondition(d, axis)[2:5, 2:5, 2:5]
+    np.testing.assert_allclose(resp, k, atol=1e-15)
+    if axis == 2:
+        assert resp[1, 1, 1] == 1.0 and resp[0, 1, 1] == 0.0 and resp[1, 0, 1] == -4 / 64
+
+
+def test_precondition_self_adjoint():
+    x = synth.random_volume(10, 1)
+    y = synth.random_volume(10, 2)
+    assert abs(np.vdot(x, O.precondition(y)) - np.vdot(O.precondition(x), y)) < 1e-12
+
+
+def test_soft_threshold():
+    x = np.array([-2.0, -0.5, 0.0, 0.3, 1.5])
+    np.testing.assert_allclose(O.soft_threshold(x, 0.5), [-1.5, 0.0, 0.0, 0.0, 1.0])
+    np.testing.assert_array_equal(O.soft_threshold(x, 0.0), x)
+
+
+# ---------------------------------------------------------------- R / P
+
+def test_restrict_prolong_invariants():
+    n = 8
+    c = np.full((n, n, n), 3.25)
+    np.testing.assert_allclose(O.restrict_volume(np.full((2 * n,) * 3, 3.25)), c)
+    np.testing.assert_allclose(O.prolong(c), np.full((2 * n,) * 3, 3.25))
+    # restrict of a fine linear function = the linear function at coarse centres
+    nf = 16
+    i = np.arange(nf)
+    xf = (i - (nf - 1) / 2) / nf
+    lin_f = 0.3 * xf[None, None, :] - 1.7 * xf[None, :, None] + 0.9 * xf[:, None, None]
+    ic = np.arange(nf // 2)
+    xc = (ic - (nf // 2 - 1) / 2) / (nf // 2)
+    lin_c = 0.3 * xc[None, None, :] - 1.7 * xc[None, :, None] + 0.9 * xc[:, None, None]
+    np.testing.assert_allclose(O.restrict_volume(lin_f), lin_c, atol=1e-14)
+    # prolongation is exact for linear functions away from the clamped edges
+    pf = O.prolong(lin_c)
+    np.testing.assert_allclose(pf[1:-1, 1:-1, 1:-1], lin_f[1:-1, 1:-1, 1:-1], atol=1e-14)
+    # the 1-D stencil: fine cells 2i, 2i+1 take 3/4 of coarse i and 1/4 of i-1, i+1
+    c1 = np.zeros((4, 4, 4))
+    c1[1, 1, 1] = 1.0
+    p1 = O.prolong(c1)
+    assert abs(p1[2, 2, 2] - 0.75 ** 3) < 1e-15
+    assert abs(p1[1, 2, 2] - 0.25 * 0.75 ** 2) < 1e-15
+    assert abs(p1[4, 2, 2] - 0.25 * 0.75 ** 2) < 1e-15
+    assert p1[0, 2, 2] == 0.0
+    b = synth.random_sino(3, 8, 6, 1)
+    rb = O.restrict_sino(b)
+    assert rb.shape == (3, 4, 3)
+    assert abs(rb[1, 2, 1] - b[1, 4:6, 2:4].mean()) < 1e-15
+
+
+# ---------------------------------------------------------------- solvers
+
+def _dense(g):
+    n = g.n
+    A = np.zeros((g.n_views * g.nv * g.nu, n ** 3))
+    for j in range(n ** 3):
+        e = np.zeros(n ** 3)
+        e[j] = 1.0
+        A[:, j] = O.project(g, e.reshape(n, n, n)).ravel()
+    return A
+
+
+def test_landweber_line_search_and_fixed_point():
+    """Eq. 2/4 with the exact line search: alpha minimises |b - P(mu + alpha d)|
+    along d, the predicted residual is the true one, and the least-squares
+    solution (numpy lstsq on the dense matrix) is a fixed point of SIRT."""
+    n = 6
+    scan = make_scan(n, nviews=16, seed=9, nu=10, nv=10)
+    g = O.level_geometry(scan, 0)
+    A = _dense(g)
+    x_true = synth.random_volume(n, 3)
+    b = (A @ x_true.ravel()).reshape(g.n_views, g.nv, g.nu) + 0.01 * synth.random_sino(
+        g.n_views, g.nv, g.nu, 4)
+    mu = np.zeros((n, n, n))
+    prev = None
+    for precond in (True, False):
+        mu = np.zeros((n, n, n))
+        for it in range(5):
+            new, st = O.landweber_step(g, mu, b, precond=precond)
+            r_new = np.sum((b - O.project(g, new)) ** 2)
+            assert abs(r_new - st["r2_pred"]) <= 1e-9 * st["r2"]
+            assert r_new <= st["r2"] * (1 + 1e-12)
+            d = (new - mu) / st["alpha"] if st["alpha"] != 0 else None
+            if d is not None:
+                for eps in (1e-3, -1e-3):
+                    alt = np.sum((b - O.project(g, mu + (st["alpha"] * (1 + eps)) * d)) ** 2)
+                    assert alt >= r_new * (1 - 1e-12)
+            mu = new
+    xs, *_ = np.linalg.lstsq(A, b.ravel(), rcond=None)
+    xs = xs.reshape(n, n, n)
+    out, st = O.landweber_step(g, xs, b, precond=False, alpha=0.5)
+    np.testing.assert_allclose(out, xs, atol=1e-9)
+
+
+def test_sirt_converges_to_least_squares():
+    """Brute force at 4^3: SIRT (Eq. 2) with a fixed alpha < 2 / |A|^2 converges
+    to numpy's least-squares solution."""
+    n = 4
+    scan = make_scan(n, nviews=10, seed=10, nu=6, nv=6)
+    g = O.level_geometry(scan, 0)
+    A = _dense(g)
+    lmax = np.linalg.norm(A, 2) ** 2
+    x_true = synth.random_volume(n, 5)
+    b = (A @ x_true.ravel()).reshape(g.n_views, g.nv, g.nu) + 0.01 * synth.random_sino(
+        g.n_views, g.nv, g.nu, 6)
+    xs, *_ = np.linalg.lstsq(A, b.ravel(), rcond=None)
+    mu = np.zeros((n, n, n))
+    s = np.linalg.svd(A, compute_uv=False)
+    iters = int(np.ceil(30.0 / (1.9 * (s[-1] ** 2) / lmax)))
+    iters = min(iters, 20000)
+    for _ in range(iters):
+        mu, _ = O.landweber_step(g, mu, b, alpha=1.9 / lmax, precond=False)
+    assert np.abs(mu.ravel() - xs).max() < 1e-6 * np.abs(xs).max()
+
+
+def test_osemtr_fixed_point_and_direction():
+    """Eq. 3: with consistent data b = P x, x is a fixed point (numerator 0);
+    from below (mu = 0.5 x) one pass moves mu towards x."""
+    n = 12
+    scan = make_scan(n, nviews=16, seed=11)
+    g = O.level_geometry(scan, 0)
+    x = 0.5 * synth.random_volume(n, 8) + 0.2
+    b = O.project(g, x)
+    out = O.osemtr_pass(g, x, b, n_subsets=4)
+    assert np.abs(out - x).max() < 1e-12
+    mu0 = 0.5 * x
+    mu1 = O.osemtr_pass(g, mu0, b, n_subsets=4)
+    r0 = np.linalg.norm(b - O.project(g, mu0))
+    r1 = np.linalg.norm(b - O.project(g, mu1))
+    assert r1 < 0.5 * r0
+
+
+def test_multigrid_single_level_is_one_landweber_step():
+    n = 8
+    scan = make_scan(n, nviews=6, seed=12)
+    g = O.level_geometry(scan, 0)
+    x = synth.random_volume(n, 9)
+    b = O.project(g, x)
+    mu0 = 0.1 * synth.random_volume(n, 10)
+    mg = O.multigrid(scan, mu0, [b], levels=1)
+    lw, _ = O.landweber_step(g, mu0, b)
+    np.testing.assert_allclose(mg, lw, rtol=0, atol=1e-13)
+
+
+def test_multigrid_structure_two_levels():
+    """Alg. 1 with two grids: the fine estimate after the coarse correction is
+    mu + Prolongate(osemtr(R mu) - R mu), then one Landweber step."""
+    n = 8
+    scan = make_scan(n, nviews=8, seed=13)
+    x = synth.random_volume(n, 11)
+    b = O.project(O.level_geometry(scan, 0), x)
+    bl = O.data_levels(b, 2)
+    mu0 = 0.2 * synth.random_volume(n, 12)
+    got = O.multigrid(scan, mu0, bl, levels=2)
+    mc = O.restrict_volume(mu0)
+    mc2 = O.osemtr_pass(O.level_geometry(scan, 1), mc, bl[1])
+    want, _ = O.landweber_step(O.level_geometry(scan, 0), mu0 + O.prolong(mc2 - mc), b)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+@pytest.mark.slow
+def test_pmgl_beats_sirt_at_equal_cost():
+    """Sec. 3 / Fig. 4: after 2 iterations preconditioned multigrid Landweber is
+    closer to the truth than SIRT with the same number of fine-grid P/B calls."""
+    n = 32
+    th, z = synth.trajectory(48, 2104)
+    nu = 48
+    scan = O.Scan(n=n, nu=nu, nv=nu, theta=th, z=z, pitch=synth.default_pitch(nu))
+    ph = synth.ellipsoids(10, 2103)
+    truth = synth.voxelize_ellipsoids(ph, n, supersample=2).numpy()
+    b = O.ellipsoid_line_integrals(O.level_geometry(scan, 0), ph)
+    mg = O.reconstruct(scan, b, iters=2, levels=2)
+    sirt = O.sirt(scan, b, iters=2)
+    e_mg = np.sqrt(np.mean((mg - truth) ** 2))
+    e_sirt = np.sqrt(np.mean((sirt - truth) ** 2))
+    assert e_mg < e_sirt, (e_mg, e_sirt)

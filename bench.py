@@ -1,0 +1,517 @@
+#!/usr/bin/env python
+"""Benchmark of the preconditioned multigrid Landweber reconstruction on one
+GB300 (replicas only across GPUs).
+
+One step = one multigrid iteration of Alg. 1 at grid 0 (restrict, recurse,
+OS-EMTR on the coarsest grid, prolongate, and on every other grid one
+preconditioned Landweber step: A with residual, A^T, the Eq. 5 filter, a
+second A for the line search, the update).  Workload: 256^3 volume of 200
+random ellipsoids plus a porous texture, 384x384 detector, 720 views on the
+space-filling trajectory, 3 grids, Poisson noise at 1e4 photons per ray; the
+data are projected from a 2x finer phantom.
+
+The value is whole-job A+A^T throughput in GUPS: voxel-view updates (n_g^3 x
+views for every A and A^T call of the step, on every grid) per second.
+`--impl reference` times the FP64 CPU oracle (A and A^T on a sample of views)
+on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A+A^T GUPS & % BW roofline; sec to RMSE≤1e-3 (learned/BF16 vs plain FP32)"
+WORKLOADS = {
+    # name: n, nu, views, levels, ellipsoids, axis range, texture, photons
+    "c2": dict(n=256, nu=384, views=720, levels=3, count=200, axis=(0.01, 0.08), texture=True,
+               photons=1e4),
+    "c1": dict(n=64, nu=96, views=90, levels=2, count=10, axis=(0.04, 0.2), texture=False, photons=0),
+}
+SEED = 2103
+FP32_LANES_PER_SM, SMS = 128, 152
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(name):
+    w = WORKLOADS[name]
+    return {"workload": f"{w['n']}^3 volume, {w['count']} ellipsoids" + (" + porous texture" if w["texture"] else "")
+            + f", {w['nu']}x{w['nu']} detector, {w['views']} space-filling views, {w['levels']} grids"
+            + (f", Poisson {w['photons']:.0e} photons/ray" if w["photons"] else ", noise-free"),
+            "n": w["n"], "detector": [w["nu"], w["nu"]], "views": w["views"], "levels": w["levels"],
+            "iteration": "Alg. 1 multigrid, Landweber with line search, OS-EMTR M=8 on the coarsest grid",
+            "l2": "inputs larger than L2 (sinogram %d MB)" % (w["views"] * w["nu"] ** 2 * 4 // 2 ** 20)}
+
+
+def units_per_step(n, views, levels):
+    """Voxel-view updates of the A / A^T calls of one multigrid iteration."""
+    u = 0
+    for g in range(levels):
+        ng = n >> g
+        if levels == 1 or g < levels - 1:
+            u += 3 * ng ** 3 * views   # A (residual), A^T, A (line search)
+        else:
+            u += 2 * ng ** 3 * views   # OS-EMTR: A and two-channel A^T over all subsets
+    return u
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of A / A^T: nonzeros of the matrix (4 bilinear taps per
+# in-volume sample), counted per ray from the plane range where the ray's
+# crossing lies inside (-1, n) on both in-plane axes
+# ---------------------------------------------------------------------------
+def count_nnz(theta, z, pitch, n, nu, nv, src_axis=2.0, src_det=4.0, device="cuda"):
+    import torch
+    h = 1.0 / n
+    ic = 0.5 * (n - 1)
+    total = 0.0
+    ju = torch.arange(nu, device=device, dtype=torch.float64) - 0.5 * (nu - 1)
+    jv = torch.arange(nv, device=device, dtype=torch.float64) - 0.5 * (nv - 1)
+    for k0 in range(0, len(theta), 32):
+        th = torch.as_tensor(theta[k0:k0 + 32], device=device, dtype=torch.float64)
+        zz = torch.as_tensor(z[k0:k0 + 32], device=device, dtype=torch.float64)
+        c, s = torch.cos(th), torch.sin(th)
+        src = torch.stack([src_axis * c, src_axis * s, zz], 1)
+        dcen = src + src_det * torch.stack([-c, -s, torch.zeros_like(c)], 1)
+        eu = torch.stack([-s, c, torch.zeros_like(c)], 1)
+        p = (dcen[:, None, None, :] + (ju[None, None, :, None] * pitch) * eu[:, None, None, :])
+        p = p.expand(-1, nv, -1, -1).clone()
+        p[..., 2] = p[..., 2] + (jv[None, :, None] * pitch)
+        w = p - src[:, None, None, :]
+        ax = (w[..., 1].abs() > w[..., 0].abs()).long()
+        wa = torch.where(ax == 1, w[..., 1], w[..., 0])
+        wb = torch.where(ax == 1, w[..., 0], w[..., 1])
+        sa = torch.where(ax == 1, src[:, 1, None, None], src[:, 0, None, None]).expand_as(wa) / h + ic
+        sb = torch.where(ax == 1, src[:, 0, None, None], src[:, 1, None, None]).expand_as(wa) / h + ic
+        sz = (src[:, 2, None, None] / h + ic).expand_as(wa)
+        lo = torch.zeros_like(wa)
+        hi = torch.full_like(wa, n - 1.0)
+        for (s0, wq) in ((sb, wb), (sz, w[..., 2])):
+            r = wq / wa
+            t1 = sa + (-1.0 - s0) / r
+            t2 = sa + (n - s0) / r
+            lo = torch.maximum(lo, torch.minimum(t1, t2))
+            hi = torch.minimum(hi, torch.maximum(t1, t2))
+        cnt = (torch.floor(hi) - torch.ceil(lo) + 1).clamp(min=0)
+        total += float(cnt.sum())
+    return 4.0 * total
+
+
+# ---------------------------------------------------------------------------
+# workload synthesis (GPU, torch + the library's projector)
+# ---------------------------------------------------------------------------
+def make_workload(name, device="cuda"):
+    import torch
+    from paper_2103_10329_gb300 import mgct, synth
+    w = WORKLOADS[name]
+    n, nu, K, L = w["n"], w["nu"], w["views"], w["levels"]
+    th, z = synth.trajectory(K, SEED + 1)
+    pitch = synth.default_pitch(nu)
+    ph = synth.ellipsoids(w["count"], SEED, axis_lo=w["axis"][0], axis_hi=w["axis"][1])
+    truth = synth.voxelize_ellipsoids(ph, n, supersample=2, device=device, dtype=torch.float32)
+    tex = synth.porous_texture(n, SEED + 3, device=device) if w["texture"] else None
+    if tex is not None:
+        truth += tex
+    # data from a phantom twice as fine (no inverse crime)
+    fine = synth.voxelize_ellipsoids(ph, 2 * n, supersample=1, device=device, dtype=torch.float32)
+    if tex is not None:
+        fine += tex.repeat_interleave(2, 0).repeat_interleave(2, 1).repeat_interleave(2, 2)
+    gf = mgct.Geometry(2 * n, nu, nu, th, z, pitch, levels=1)
+    b = mgct.project(gf, fine)
+    del fine
+    gf.close()
+    if w["photons"]:
+        b = synth.poisson_log_data(b, w["photons"], SEED + 2)
+    torch.cuda.synchronize()
+    g = mgct.Geometry(n, nu, nu, th, z, pitch, levels=L)
+    return dict(geom=g, b=b.contiguous(), truth=truth, theta=th, z=z, pitch=pitch, n=n, nu=nu, views=K,
+                levels=L)
+
+
+def roi_rmse(vol, truth):
+    import torch
+    n = truth.shape[0]
+    c = (torch.arange(n, device=truth.device, dtype=torch.float32) - (n - 1) / 2) / n
+    r2 = c[None, :, None] ** 2 + c[None, None, :] ** 2
+    m = (r2 <= (0.45) ** 2) & (c.abs()[:, None, None] <= 0.45)
+    d = (vol - truth)[m]
+    rng = float(truth.max() - truth.min())
+    return float(torch.sqrt(torch.mean(d.double() ** 2))) / rng
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(name, target_s=15.0, vol=None, views_cap=None):
+    """A and A^T of the FP64 oracle at grid 0 on a sample of views; returns
+    (GUPS, seconds, views used, threads)."""
+    import oracle as O
+    from paper_2103_10329_gb300 import synth
+    w = WORKLOADS[name]
+    n, nu, K = w["n"], w["nu"], w["views"]
+    th, z = synth.trajectory(K, SEED + 1)
+    scan = O.Scan(n=n, nu=nu, nv=nu, theta=th, z=z, pitch=synth.default_pitch(nu))
+    g = O.level_geometry(scan, 0)
+    if vol is None:
+        vol = synth.random_volume(n, SEED)
+
+    def run(cnt):
+        gs = g.subset(np.arange(cnt))
+        t0 = time.perf_counter()
+        y = O.project(gs, vol)
+        t1 = time.perf_counter()
+        O.backproject(gs, y)
+        t2 = time.perf_counter()
+        return t2 - t0
+
+    cnt = min(4, K)
+    t = run(cnt)
+    if views_cap is None:
+        cnt2 = int(max(cnt, min(K, cnt * target_s / max(t, 1e-3))))
+    else:
+        cnt2 = min(views_cap, K)
+    t = run(cnt2)
+    gups = 2.0 * n ** 3 * cnt2 / t / 1e9
+    return gups, t, cnt2, O.num_threads()
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    name = args.workload
+    w = WORKLOADS[name]
+    import oracle as O
+    O.build()
+    from paper_2103_10329_gb300 import synth
+    vol = synth.random_volume(w["n"], SEED)
+    # one step = oracle A + A^T on a fixed sample of views
+    per_step_views = args.ref_views
+    vals = []
+    for i in range(args.warmup + args.steps):
+        gups, t, cnt, thr = oracle_sample(name, vol=vol, views_cap=per_step_views)
+        if i >= args.warmup:
+            vals.append((gups, t))
+    tot_t = sum(t for _, t in vals)
+    units = 2.0 * w["n"] ** 3 * per_step_views * len(vals)
+    value = units / tot_t / 1e9
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(name),
+            "cpu_baseline": {"value": value, "unit": "GUPS", "cores": thr, "host_cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle A and A^T at grid 0 on {per_step_views} of {w['views']} "
+                                       f"views per step"},
+            "e2e": {"value": value, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def traffic_record(kernel):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json, if the
+    kernel sources are unchanged since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p)).get(kernel)
+        if not rec:
+            return None
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != rec["sha256"]:
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_2103_10329_gb300 import build, mgct
+    if world > 1:
+        import torch.distributed as dist
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    W = make_workload(args.workload)
+    g, b, truth = W["geom"], W["b"], W["truth"]
+    n, K, L = W["n"], W["views"], W["levels"]
+    rec = mgct.Reconstructor(g)
+    rec.prepare(b)
+    vol = torch.zeros((n, n, n), device=dev, dtype=torch.float32)
+    units = units_per_step(n, K, L)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        rec.iterate(vol)
+    torch.cuda.synchronize()
+    # ---- device-resident timed region
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    mgct.trace_enable(True)
+    mgct.launch_count(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        rec.iterate(vol)
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = mgct.launch_count()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    trace = mgct.trace_read()
+    mgct.trace_enable(False)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms)
+    total_units = sum_over_ranks(units * args.steps)
+    value = total_units / (ms_max / 1e3) / 1e9
+
+    # ---- per-kernel work and the dominant kernel's roofline
+    nnz = [count_nnz(W["theta"], W["z"], W["pitch"], n >> lv, W["nu"] >> lv, W["nu"] >> lv) for lv in range(L)]
+    flops = {"project": 0.0, "backproject": 0.0}
+    for lv in range(L):
+        if L == 1 or lv < L - 1:
+            flops["project"] += 2 * 2 * nnz[lv]
+            flops["backproject"] += 2 * nnz[lv]
+        else:
+            flops["project"] += 2 * nnz[lv]
+            flops["backproject"] += 2 * 2 * nnz[lv]
+    kern_ms = {k: v[0] for k, v in trace.items() if v[1]}
+    traced = sum(kern_ms.values())
+    dom = max(kern_ms, key=kern_ms.get)
+    sm_clock = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12  # TFLOP/s
+    kernels = {}
+    for k, (t, c) in trace.items():
+        if not c:
+            continue
+        e = {"ms_per_step": t / args.steps, "launches_per_step": c / args.steps, "share": t / traced}
+        if k in flops:
+            e["tflops_alg"] = flops[k] * args.steps / (t / 1e3) / 1e12
+            # voxel-view updates done by this kernel per step: on the Landweber
+            # grids two projections and one back-projection, on the coarsest
+            # grid one of each (OS-EMTR)
+            vv = 0
+            for lv in range(L):
+                calls = (2 if k == "project" else 1) if (L == 1 or lv < L - 1) else 1
+                vv += calls * (n >> lv) ** 3 * K
+            e["gups"] = vv * args.steps / (t / 1e3) / 1e9
+        kernels[k] = e
+    if dom in flops:
+        achieved = flops[dom] * args.steps / (kern_ms[dom] / 1e3) / 1e12
+        tr = traffic_record("k_" + dom)
+        roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_clock:.0f} MHz",
+                "work": "2 flop per nonzero of A (4 bilinear taps per in-volume sample)",
+                "traffic": tr["bytes_per_launch"] if tr else None}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.empty(b.shape, dtype=torch.float32, pin_memory=True)
+        hb.copy_(b)
+        hv = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
+        bdev = torch.empty_like(b)
+        stream = torch.cuda.current_stream()
+        for _ in range(2):
+            bdev.copy_(hb, non_blocking=True)
+            rec.prepare(bdev)
+            rec.iterate(vol)
+            hv.copy_(vol, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            bdev.copy_(hb, non_blocking=True)
+            rec.prepare(bdev)
+            rec.iterate(vol)
+            hv.copy_(vol, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": total_units / (ems / 1e3) / 1e9, "unit": "GUPS", "ms_per_step": ems / args.steps,
+               "h2d_bytes_per_step": hb.numel() * 4, "d2h_bytes_per_step": hv.numel() * 4}
+        rec.prepare(b)
+
+    # ---- time to accuracy (plain FP32), PMGL vs SIRT at equal fine-grid cost
+    tta = None
+    if not args.no_tta and rank == 0:
+        v = torch.zeros_like(vol)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        rec.iterate(v)
+        rec.iterate(v)
+        s1.record()
+        torch.cuda.synchronize()
+        pm_ms = s0.elapsed_time(s1)
+        e_pm = roi_rmse(v, truth)
+        vs = torch.zeros_like(vol)
+        ws = mgct.workspace(g, mgct.WS_LANDWEBER, 0)
+        s0.record()
+        for _ in range(2):
+            mgct.landweber_step(g, vs, b, precond=False, ws=ws)
+        s1.record()
+        torch.cuda.synchronize()
+        e_si = roi_rmse(vs, truth)
+        tta = {"pmgl_2iter_ms": pm_ms, "pmgl_2iter_rmse_roi": e_pm, "sirt_2iter_ms": s0.elapsed_time(s1),
+               "sirt_2iter_rmse_roi": e_si, "rmse_def": "RMS(mu - truth) / range(truth) over r <= 0.9R, |z| <= 0.9R"}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle as O
+        O.build()
+        gups, t, cnt, thr = oracle_sample(args.workload, target_s=args.cpu_seconds,
+                                          vol=truth.double().cpu().numpy())
+        cpu = {"value": gups, "unit": "GUPS", "cores": thr, "kind": "oracle",
+               "sample": f"FP64 oracle A and A^T at grid 0 on {cnt} of {K} views ({t:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(workload_config(args.workload), parallelism=f"replicas x{world}"),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "kernels": kernels, "time_to_accuracy": tta}
+        print(json.dumps(line), flush=True)
+    g.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mgct", choices=["mgct", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tta", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-views", type=int, default=8)
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        reference_arm(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    gpu_arm(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

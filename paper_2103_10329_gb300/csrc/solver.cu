@@ -1,0 +1,393 @@
+// C-ABI entry points: projector, back-projector, filters, grid transfer, and
+// the solvers built from them -- the preconditioned Landweber step (Eq. 4,
+// Eq. 2 without the filter), the OS-EMTR pass (Eq. 3) and the recursive
+// multigrid iteration (Alg. 1).  The solvers run entirely on the stream: the
+// step size is computed on the device and read there by the update kernel,
+// so an iteration issues no host synchronisation.
+#include <cstring>
+
+#include "backproject.cuh"
+#include "common.cuh"
+#include "project.cuh"
+
+namespace mgct {
+
+int launch_precondition(int n, int slice_axis, const float *in, float *out, cudaStream_t s);
+int launch_restrict_volume(int n_fine, const float *in, float *out, cudaStream_t s);
+int launch_restrict_sino(int k, int nv, int nu, const float *in, float *out, cudaStream_t s);
+int launch_prolong_add(int nc, const float *cn, const float *co, float *fine, cudaStream_t s);
+int launch_step_size(const double *sums, const double *r2, double fixed_alpha, double *stats, cudaStream_t s);
+int launch_update(size_t count, float *mu, const float *d, const double *alpha, float lam, cudaStream_t s);
+int launch_em_update(size_t count, float *mu, const float *nd, double *part, cudaStream_t s);
+int launch_fill(size_t count, float *x, float v, cudaStream_t s);
+int launch_copy(size_t count, const float *in, float *out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Workspace carving
+// ---------------------------------------------------------------------------
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static size_t vox(const LevelInfo &L) { return (size_t)L.n * L.n * L.n; }
+static size_t sino_elems(const mgct_geom *g, const LevelInfo &L) {
+    return (size_t)g->desc.n_views * L.nv * L.nu;
+}
+static size_t proj_blocks(const mgct_geom *g, const LevelInfo &L) {
+    return (size_t)((L.nu + PJ_BX - 1) / PJ_BX) * ((L.nv + PJ_BY - 1) / PJ_BY) * g->desc.n_views;
+}
+
+struct LWSpace {
+    float *r, *grad, *d, *muT;
+    double *part, *sums, *stats;  // sums: [0] r2, [1] <r,Ad>, [2] |Ad|^2 ; stats: 4
+};
+
+static LWSpace carve_lw(const mgct_geom *g, int level, Carver &c) {
+    const LevelInfo &L = g->lev[level];
+    LWSpace w;
+    w.r = c.take<float>(sino_elems(g, L));
+    w.grad = c.take<float>(vox(L));
+    w.d = c.take<float>(vox(L));
+    w.muT = c.take<float>(vox(L));
+    w.part = c.take<double>(2 * proj_blocks(g, L) + 64);
+    w.sums = c.take<double>(8);
+    w.stats = c.take<double>(8);
+    return w;
+}
+
+struct EMSpace {
+    float2 *c2;
+    float *nd, *muT;
+    double *part;
+};
+
+static EMSpace carve_em(const mgct_geom *g, int level, Carver &c) {
+    const LevelInfo &L = g->lev[level];
+    EMSpace w;
+    w.c2 = c.take<float2>(sino_elems(g, L));  // worst case: one subset holding every view
+    w.nd = c.take<float>(2 * vox(L));
+    w.muT = c.take<float>(vox(L));
+    w.part = c.take<double>(1024);
+    return w;
+}
+
+struct MGSpace {
+    float *b[8], *mu[8], *old[8];
+    float *pi;
+    int prepared_flag;
+    void *lw_base, *em_base;
+    size_t lw_bytes, em_bytes;
+};
+
+static MGSpace carve_mg(const mgct_geom *g, Carver &c) {
+    MGSpace m;
+    std::memset(&m, 0, sizeof(m));
+    for (int l = 1; l < g->levels; ++l) {
+        m.b[l] = c.take<float>(sino_elems(g, g->lev[l]));
+        m.mu[l] = c.take<float>(vox(g->lev[l]));
+        m.old[l] = c.take<float>(vox(g->lev[l]));
+    }
+    int lc = g->levels - 1;
+    m.pi = g->levels > 1 ? c.take<float>(sino_elems(g, g->lev[lc])) : nullptr;
+    // sub-workspaces: Landweber sized for grid 0 (the largest), OS-EMTR for the coarsest
+    Carver probe(nullptr);
+    carve_lw(g, 0, probe);
+    m.lw_bytes = probe.off;
+    m.lw_base = c.take<char>(m.lw_bytes);
+    Carver probe2(nullptr);
+    carve_em(g, lc, probe2);
+    m.em_bytes = probe2.off;
+    m.em_base = c.take<char>(m.em_bytes);
+    return m;
+}
+
+static size_t ws_bytes(const mgct_geom *g, int op, int level) {
+    Carver c(nullptr);
+    if (op == MGCT_WS_LANDWEBER) carve_lw(g, level, c);
+    else if (op == MGCT_WS_OSEMTR) carve_em(g, level, c);
+    else carve_mg(g, c);
+    return c.off + 256;
+}
+
+static int check_ws(const mgct_geom *g, int op, int level, const void *ws, size_t bytes) {
+    MGCT_TRY(check_ptr(ws, "workspace"));
+    if (reinterpret_cast<uintptr_t>(ws) % 256)
+        return set_error(MGCT_EALIGN, "workspace must be 256-byte aligned");
+    size_t need = ws_bytes(g, op, level);
+    if (bytes < need)
+        return set_error(MGCT_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+    return MGCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solver steps
+// ---------------------------------------------------------------------------
+static int landweber(const mgct_geom *g, int level, float *mu, const float *b, void *ws,
+                     const mgct_lw_opts &o, mgct_lw_stats *stats_out, cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    Carver c(ws);
+    LWSpace w = carve_lw(g, level, c);
+    const int K = g->desc.n_views;
+    const size_t nv3 = vox(L);
+    double *stats = stats_out ? reinterpret_cast<double *>(stats_out) : w.stats;
+    MGCT_TRY(check_cuda(cudaMemsetAsync(w.sums, 0, 8 * sizeof(double), s), "memset"));
+    // r = b - A mu, |r|^2
+    MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
+    int nb = 0;
+    EpiResidual<float> er{w.r, b, w.part, L.nu, L.nv};
+    MGCT_TRY(launch_project<float>(g, level, 0, K, 1, mu, w.muT, er, s, &nb));
+    MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
+    // d = p * A^T r   (or A^T r for SIRT)
+    MGCT_TRY(launch_backproject<1, float>(g, level, 0, K, 1, w.r, w.grad, 0, s));
+    float *d = w.grad, *dT = w.d;
+    if (o.precondition) {
+        MGCT_TRY(launch_precondition(L.n, g->desc.p_slice_axis, w.grad, w.d, s));
+        d = w.d;
+        dT = w.grad;  // the gradient is no longer needed
+    }
+    if (!(o.alpha > 0.0)) {
+        // exact line search along d: <r, A d>, |A d|^2
+        MGCT_TRY(launch_transpose_xy<float>(L.n, d, dT, s));
+        EpiDualDot<float> ed{w.r, w.part, L.nu, L.nv};
+        MGCT_TRY(launch_project<float>(g, level, 0, K, 1, d, dT, ed, s, &nb));
+        MGCT_TRY(launch_sum_partials(w.part, nb, 2, w.sums + 1, s));
+    }
+    MGCT_TRY(launch_step_size(w.sums + 1, w.sums + 0, o.alpha > 0.0 ? o.alpha : 0.0, stats, s));
+    MGCT_TRY(launch_update(nv3, mu, d, stats, (float)o.lambda, s));
+    (void)nv3;
+    return MGCT_OK;
+}
+
+static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *b, const float *pi, void *ws,
+                  cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    Carver c(ws);
+    EMSpace w = carve_em(g, level, c);
+    const int K = g->desc.n_views;
+    const size_t nv3 = vox(L);
+    for (int m = 0; m < M; ++m) {
+        int cnt = (K - m + M - 1) / M;
+        if (cnt <= 0) continue;
+        MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
+        EpiEMTerms e{w.c2, b, pi, L.nu, L.nv};
+        MGCT_TRY(launch_project<float>(g, level, m, cnt, M, mu, w.muT, e, s));
+        MGCT_TRY(launch_backproject<2, float2>(g, level, m, cnt, M, w.c2, w.nd, 0, s));
+        MGCT_TRY(launch_em_update(nv3, mu, w.nd, w.part, s));
+    }
+    return MGCT_OK;
+}
+
+static int multigrid_level(const mgct_geom *g, int level, float *mu, const MGSpace &m, const float *b0,
+                           const mgct_lw_opts &o, mgct_lw_stats *stats, cudaStream_t s) {
+    const int Lc = g->levels;
+    if (level + 1 < Lc) {
+        const int nf = g->lev[level].n;
+        float *mc = m.mu[level + 1], *oc = m.old[level + 1];
+        MGCT_TRY(launch_restrict_volume(nf, mu, mc, s));
+        MGCT_TRY(launch_copy(vox(g->lev[level + 1]), mc, oc, s));
+        if (level + 1 < Lc - 1) {
+            MGCT_TRY(multigrid_level(g, level + 1, mc, m, b0, o, stats, s));
+        } else {
+            int M = o.n_subsets > 0 ? o.n_subsets : 8;
+            MGCT_TRY(osemtr(g, level + 1, M, mc, m.b[level + 1], m.pi, m.em_base, s));
+        }
+        MGCT_TRY(launch_prolong_add(g->lev[level + 1].n, mc, oc, mu, s));
+    }
+    const float *b = level == 0 ? b0 : m.b[level];
+    return landweber(g, level, mu, b, m.lw_base, o, stats ? stats + level : nullptr, s);
+}
+
+static int check_opts(const mgct_lw_opts *o) {
+    if (!o) return set_error(MGCT_EINVAL, "opts is NULL");
+    if (o->learned_corr) return set_error(MGCT_EINVAL, "learned_corr is reserved and must be NULL");
+    if (!(o->lambda >= 0.0)) return set_error(MGCT_EINVAL, "lambda must be >= 0");
+    if (o->n_subsets < 0) return set_error(MGCT_EINVAL, "n_subsets must be >= 0");
+    return MGCT_OK;
+}
+
+}  // namespace mgct
+
+using namespace mgct;
+
+extern "C" {
+
+int mgct_project(const mgct_geom *g, int level, int view0, int nviews, int stride, const void *vol, mgct_dtype vt,
+                 void *out, mgct_dtype ot, const float *b, double *sumsq, mgct_stream stream) {
+    MGCT_TRY(validate_level(g, level));
+    MGCT_TRY(validate_views(g, view0, nviews, stride));
+    MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(out, "out", nviews == 0));
+    MGCT_TRY(check_ptr(b, "b", true));
+    if (sumsq && reinterpret_cast<uintptr_t>(sumsq) % 8) return set_error(MGCT_EALIGN, "sumsq must be 8-byte aligned");
+    if (vt < MGCT_F32 || vt > MGCT_F16 || ot < MGCT_F32 || ot > MGCT_F16)
+        return set_error(MGCT_EDTYPE, "dtype must be MGCT_F32, MGCT_BF16 or MGCT_F16");
+    if (sumsq && !b) return set_error(MGCT_EINVAL, "sumsq needs b (it is the residual norm)");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const LevelInfo &L = g->lev[level];
+    if (nviews == 0) {
+        if (sumsq) MGCT_TRY(check_cuda(cudaMemsetAsync(sumsq, 0, sizeof(double), s), "memset"));
+        return MGCT_OK;
+    }
+    int nb = 0;
+    double *part = sumsq ? g->d_scratch_part : nullptr;
+    auto run = [&](auto vtag, auto otag) -> int {
+        using VT = decltype(vtag);
+        using OT = decltype(otag);
+        const VT *v = static_cast<const VT *>(vol);
+        VT *vT = static_cast<VT *>(g->d_scratch_vol);
+        MGCT_TRY(launch_transpose_xy<VT>(L.n, v, vT, s));
+        if (b) {
+            EpiResidual<OT> e{static_cast<OT *>(out), b, part, L.nu, L.nv};
+            return launch_project<VT>(g, level, view0, nviews, stride, v, vT, e, s, &nb);
+        }
+        EpiStore<OT> e{static_cast<OT *>(out), L.nu, L.nv};
+        return launch_project<VT>(g, level, view0, nviews, stride, v, vT, e, s, &nb);
+    };
+    auto run_v = [&](auto vtag) -> int {
+        switch (ot) {
+            case MGCT_F32: return run(vtag, float());
+            case MGCT_BF16: return run(vtag, __nv_bfloat16());
+            default: return run(vtag, __half());
+        }
+    };
+    int st;
+    switch (vt) {
+        case MGCT_F32: st = run_v(float()); break;
+        case MGCT_BF16: st = run_v(__nv_bfloat16()); break;
+        default: st = run_v(__half()); break;
+    }
+    MGCT_TRY(st);
+    if (sumsq) MGCT_TRY(launch_sum_partials(part, nb, 1, sumsq, s));
+    return MGCT_OK;
+}
+
+int mgct_backproject(const mgct_geom *g, int level, int view0, int nviews, int stride, const void *sino,
+                     mgct_dtype st, float *vol_out, int accumulate, mgct_stream stream) {
+    MGCT_TRY(validate_level(g, level));
+    MGCT_TRY(validate_views(g, view0, nviews, stride));
+    MGCT_TRY(check_ptr(sino, "sino", nviews == 0));
+    MGCT_TRY(check_ptr(vol_out, "vol_out"));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (st) {
+        case MGCT_F32:
+            return launch_backproject<1, float>(g, level, view0, nviews, stride, static_cast<const float *>(sino),
+                                                vol_out, accumulate, s);
+        case MGCT_BF16:
+            return launch_backproject<1, __nv_bfloat16>(g, level, view0, nviews, stride,
+                                                        static_cast<const __nv_bfloat16 *>(sino), vol_out,
+                                                        accumulate, s);
+        case MGCT_F16:
+            return launch_backproject<1, __half>(g, level, view0, nviews, stride, static_cast<const __half *>(sino),
+                                                 vol_out, accumulate, s);
+        default: return set_error(MGCT_EDTYPE, "dtype must be MGCT_F32, MGCT_BF16 or MGCT_F16");
+    }
+}
+
+int mgct_precondition(const mgct_geom *g, int level, const float *in, float *out, mgct_stream stream) {
+    MGCT_TRY(validate_level(g, level));
+    MGCT_TRY(check_ptr(in, "in"));
+    MGCT_TRY(check_ptr(out, "out"));
+    if (in == out) return set_error(MGCT_EINVAL, "in and out must not overlap");
+    return launch_precondition(g->lev[level].n, g->desc.p_slice_axis, in, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgct_restrict_volume(int n_fine, const float *in, float *out, mgct_stream stream) {
+    if (n_fine < 2 || n_fine % 2 || n_fine > 2048) return set_error(MGCT_ESHAPE, "n_fine must be even, 2..2048");
+    MGCT_TRY(check_ptr(in, "in"));
+    MGCT_TRY(check_ptr(out, "out"));
+    return launch_restrict_volume(n_fine, in, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgct_restrict_sino(int k, int nv, int nu, const float *in, float *out, mgct_stream stream) {
+    if (k < 1 || nv < 2 || nu < 2 || nv % 2 || nu % 2) return set_error(MGCT_ESHAPE, "k >= 1, nv and nu even");
+    MGCT_TRY(check_ptr(in, "in"));
+    MGCT_TRY(check_ptr(out, "out"));
+    return launch_restrict_sino(k, nv, nu, in, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgct_prolong_add(int n_coarse, const float *cn, const float *co, float *fine, mgct_stream stream) {
+    if (n_coarse < 1 || n_coarse > 1024) return set_error(MGCT_ESHAPE, "n_coarse must be 1..1024");
+    MGCT_TRY(check_ptr(cn, "coarse_new"));
+    MGCT_TRY(check_ptr(co, "coarse_old"));
+    MGCT_TRY(check_ptr(fine, "fine"));
+    return launch_prolong_add(n_coarse, cn, co, fine, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t mgct_workspace_bytes(const mgct_geom *g, int op, int level) {
+    if (!g || op < 0 || op > 2) return 0;
+    if (op != MGCT_WS_MULTIGRID && (level < 0 || level >= g->levels)) return 0;
+    return ws_bytes(g, op, level);
+}
+
+int mgct_landweber_step(const mgct_geom *g, int level, float *vol, const float *b, void *ws, size_t bytes,
+                        const mgct_lw_opts *o, mgct_lw_stats *stats, mgct_stream stream) {
+    MGCT_TRY(validate_level(g, level));
+    MGCT_TRY(check_opts(o));
+    MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(b, "b"));
+    MGCT_TRY(check_ptr(stats, "stats", true));
+    MGCT_TRY(check_ws(g, MGCT_WS_LANDWEBER, level, ws, bytes));
+    return landweber(g, level, vol, b, ws, *o, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgct_osemtr_pass(const mgct_geom *g, int level, int n_subsets, float *vol, const float *b, const float *pi,
+                     void *ws, size_t bytes, mgct_stream stream) {
+    MGCT_TRY(validate_level(g, level));
+    if (n_subsets < 1 || n_subsets > g->desc.n_views) return set_error(MGCT_EINVAL, "n_subsets must be 1..n_views");
+    MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(b, "b"));
+    MGCT_TRY(check_ptr(pi, "pi"));
+    MGCT_TRY(check_ws(g, MGCT_WS_OSEMTR, level, ws, bytes));
+    return osemtr(g, level, n_subsets, vol, b, pi, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgct_multigrid_prepare(const mgct_geom *g, const float *b, void *ws, size_t bytes, mgct_stream stream) {
+    if (!g) return set_error(MGCT_EINVAL, "geometry handle is NULL");
+    MGCT_TRY(check_ptr(b, "b"));
+    MGCT_TRY(check_ws(g, MGCT_WS_MULTIGRID, 0, ws, bytes));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Carver c(ws);
+    MGSpace m = carve_mg(g, c);
+    const int K = g->desc.n_views;
+    const float *prev = b;
+    for (int l = 1; l < g->levels; ++l) {
+        const LevelInfo &F = g->lev[l - 1];
+        MGCT_TRY(launch_restrict_sino(K, F.nv, F.nu, prev, m.b[l], s));
+        prev = m.b[l];
+    }
+    if (g->levels > 1) {
+        // PI = A 1 on the coarsest grid (Eq. 3: projected support length)
+        int lc = g->levels - 1;
+        const LevelInfo &C = g->lev[lc];
+        float *ones = m.mu[lc], *onesT = m.old[lc];
+        MGCT_TRY(launch_fill(vox(C), ones, 1.0f, s));
+        MGCT_TRY(launch_fill(vox(C), onesT, 1.0f, s));
+        EpiStore<float> e{m.pi, C.nu, C.nv};
+        MGCT_TRY(launch_project<float>(g, lc, 0, K, 1, ones, onesT, e, s));
+    }
+    return MGCT_OK;
+}
+
+int mgct_multigrid_iteration(const mgct_geom *g, float *vol, const float *b, void *ws, size_t bytes,
+                             const mgct_lw_opts *o, mgct_lw_stats *stats, mgct_stream stream) {
+    if (!g) return set_error(MGCT_EINVAL, "geometry handle is NULL");
+    MGCT_TRY(check_opts(o));
+    MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(b, "b"));
+    MGCT_TRY(check_ptr(stats, "stats", true));
+    MGCT_TRY(check_ws(g, MGCT_WS_MULTIGRID, 0, ws, bytes));
+    Carver c(ws);
+    MGSpace m = carve_mg(g, c);
+    return multigrid_level(g, 0, vol, m, b, *o, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,345 @@
+// Streaming volume and sinogram kernels: transpose, the Eq. 5 preconditioner,
+// restriction and prolongation (Alg. 1), the Landweber update with soft
+// thresholding, and deterministic float64 reductions.  All are bound by HBM
+// bandwidth; each reads and writes its arrays once with coalesced accesses.
+#include "common.cuh"
+
+namespace mgct {
+
+// ---------------------------------------------------------------------------
+// vol [z][y][x] -> volT [z][x][y], 32x32 tiles through shared memory
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose_xy(int n, const T *__restrict__ in, T *__restrict__ out) {
+    __shared__ T tile[32][33];
+    const int z = blockIdx.z;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const size_t slab = (size_t)z * n * n;
+    for (int dy = threadIdx.y; dy < 32; dy += 8) {
+        int x = x0 + threadIdx.x, y = y0 + dy;
+        if (x < n && y < n) tile[dy][threadIdx.x] = in[slab + (size_t)y * n + x];
+    }
+    __syncthreads();
+    for (int dx = threadIdx.y; dx < 32; dx += 8) {
+        int y = y0 + threadIdx.x, x = x0 + dx;
+        if (x < n && y < n) out[slab + (size_t)x * n + y] = tile[threadIdx.x][dx];
+    }
+}
+
+template <typename T>
+int launch_transpose_xy(int n, const T *in, T *out, cudaStream_t s) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32, n);
+    MGCT_KERNEL(KK_TRANSPOSE, s, k_transpose_xy<T><<<grid, dim3(32, 8), 0, s>>>(n, in, out));
+    return MGCT_OK;
+}
+template int launch_transpose_xy<float>(int, const float *, float *, cudaStream_t);
+template int launch_transpose_xy<__nv_bfloat16>(int, const __nv_bfloat16 *, __nv_bfloat16 *, cudaStream_t);
+template int launch_transpose_xy<__half>(int, const __half *, __half *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Eq. 5 stencil: out = p * in, zero padding.  Block = 32 x 8 columns; each
+// thread walks ZB planes along z with three rolling halo planes in shared
+// memory, so every input element is read from HBM about once.
+// ---------------------------------------------------------------------------
+struct Stencil27 {
+    float c[27];  // [dz][dy][dx]
+};
+
+constexpr int ST_BX = 32, ST_BY = 8, ST_ZB = 16;
+
+__global__ void __launch_bounds__(ST_BX *ST_BY)
+    k_precondition(int n, Stencil27 K, const float *__restrict__ in, float *__restrict__ out) {
+    __shared__ float pl[3][ST_BY + 2][ST_BX + 2];
+    const int x0 = blockIdx.x * ST_BX, y0 = blockIdx.y * ST_BY, z0 = blockIdx.z * ST_ZB;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * ST_BX;
+    const size_t nn = (size_t)n * n;
+    auto load_plane = [&](int slot, int z) {
+        for (int t = tid; t < (ST_BY + 2) * (ST_BX + 2); t += ST_BX * ST_BY) {
+            int ly = t / (ST_BX + 2), lx = t % (ST_BX + 2);
+            int x = x0 + lx - 1, y = y0 + ly - 1;
+            float v = 0.0f;
+            if (z >= 0 && z < n && x >= 0 && x < n && y >= 0 && y < n) v = __ldg(in + z * nn + (size_t)y * n + x);
+            pl[slot][ly][lx] = v;
+        }
+    };
+    load_plane(0, z0 - 1);
+    load_plane(1, z0);
+    const int zend = min(n, z0 + ST_ZB);
+    for (int z = z0; z < zend; ++z) {
+        const int sm = (z - z0) % 3, s0 = (z - z0 + 1) % 3, sp = (z - z0 + 2) % 3;
+        // slots: sm holds z-1, s0 holds z, sp receives z+1
+        load_plane(sp, z + 1);
+        __syncthreads();
+        const int x = x0 + tx, y = y0 + ty;
+        if (x < n && y < n) {
+            float acc = 0.0f;
+            const int sl[3] = {sm, s0, sp};
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+                        acc = fmaf(K.c[(dz * 3 + dy) * 3 + dx], pl[sl[dz]][ty + dy][tx + dx], acc);
+            out[z * nn + (size_t)y * n + x] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+static Stencil27 eq5_stencil(int slice_axis) {
+    // Eq. 5, the printed order: three 3x3 matrices (outer index = slice)
+    static const float P[3][3][3] = {{{-1, -1, -1}, {-1, 0, -1}, {-1, -1, -1}},
+                                     {{-8, -4, -8}, {-4, 64, -4}, {-8, -4, -8}},
+                                     {{-1, -1, -1}, {-1, 0, -1}, {-1, -1, -1}}};
+    Stencil27 K;
+    for (int dz = 0; dz < 3; ++dz)
+        for (int dy = 0; dy < 3; ++dy)
+            for (int dx = 0; dx < 3; ++dx) {
+                float v;
+                if (slice_axis == 2) v = P[dz][dy][dx];
+                else if (slice_axis == 0) v = P[dx][dz][dy];
+                else v = P[dy][dz][dx];
+                K.c[(dz * 3 + dy) * 3 + dx] = v / 64.0f;
+            }
+    return K;
+}
+
+int launch_precondition(int n, int slice_axis, const float *in, float *out, cudaStream_t s) {
+    dim3 grid((n + ST_BX - 1) / ST_BX, (n + ST_BY - 1) / ST_BY, (n + ST_ZB - 1) / ST_ZB);
+    MGCT_KERNEL(KK_PRECONDITION, s, k_precondition<<<grid, dim3(ST_BX, ST_BY), 0, s>>>(n, eq5_stencil(slice_axis), in, out));
+    return MGCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Restriction (2x2x2 mean of mu, 2x2 mean of b) and prolongation
+// ---------------------------------------------------------------------------
+__global__ void k_restrict_volume(int nc, const float2 *__restrict__ in, float *__restrict__ out) {
+    const size_t total = (size_t)nc * nc * nc;
+    const int nf2 = nc;  // fine row length in float2 units
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(t % nc);
+        int y = (int)((t / nc) % nc);
+        int z = (int)(t / ((size_t)nc * nc));
+        float s = 0.0f;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                float2 v = __ldg(in + ((size_t)(2 * z + dz) * (2 * nc) + (2 * y + dy)) * nf2 + x);
+                s += v.x + v.y;
+            }
+        out[t] = 0.125f * s;
+    }
+}
+
+__global__ void k_restrict_sino(int k, int nvc, int nuc, const float2 *__restrict__ in, float *__restrict__ out) {
+    const size_t total = (size_t)k * nvc * nuc;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        int u = (int)(t % nuc);
+        size_t rest = t / nuc;
+        int v = (int)(rest % nvc);
+        size_t view = rest / nvc;
+        const float2 *row = in + (view * (2 * nvc) + 2 * v) * nuc;
+        float2 a = __ldg(row + u), b = __ldg(row + nuc + u);
+        out[t] = 0.25f * ((a.x + a.y) + (b.x + b.y));
+    }
+}
+
+// fine[2n]^3 += P(new - old): per axis the fine cell 2i takes 3/4 of coarse i
+// and 1/4 of coarse i-1, the cell 2i+1 3/4 of i and 1/4 of i+1 (clamped).
+__global__ void k_prolong_add(int nc, const float *__restrict__ cn, const float *__restrict__ co,
+                              float *__restrict__ fine) {
+    const int nf = 2 * nc;
+    const size_t total = (size_t)nf * nf * nf;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        int fx = (int)(t % nf);
+        int fy = (int)((t / nf) % nf);
+        int fz = (int)(t / ((size_t)nf * nf));
+        int ix = fx >> 1, iy = fy >> 1, iz = fz >> 1;
+        int jx = min(max(ix + ((fx & 1) ? 1 : -1), 0), nc - 1);
+        int jy = min(max(iy + ((fy & 1) ? 1 : -1), 0), nc - 1);
+        int jz = min(max(iz + ((fz & 1) ? 1 : -1), 0), nc - 1);
+        const int xs[2] = {ix, jx}, ys[2] = {iy, jy}, zs[2] = {iz, jz};
+        const float w[2] = {0.75f, 0.25f};
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    size_t ci = ((size_t)zs[a] * nc + ys[b]) * nc + xs[c];
+                    acc = fmaf(w[a] * w[b] * w[c], __ldg(cn + ci) - __ldg(co + ci), acc);
+                }
+        fine[t] += acc;
+    }
+}
+
+static int grid_for(size_t total, int threads = 256) {
+    size_t b = (total + threads - 1) / threads;
+    if (b > 152 * 64) b = 152 * 64;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+int launch_restrict_volume(int n_fine, const float *in, float *out, cudaStream_t s) {
+    int nc = n_fine / 2;
+    MGCT_KERNEL(KK_GRID, s, k_restrict_volume<<<grid_for((size_t)nc * nc * nc), 256, 0, s>>>(nc, reinterpret_cast<const float2 *>(in), out));
+    return MGCT_OK;
+}
+
+int launch_restrict_sino(int k, int nv, int nu, const float *in, float *out, cudaStream_t s) {
+    MGCT_KERNEL(KK_GRID, s, k_restrict_sino<<<grid_for((size_t)k * (nv / 2) * (nu / 2)), 256, 0, s>>>(
+        k, nv / 2, nu / 2, reinterpret_cast<const float2 *>(in), out));
+    return MGCT_OK;
+}
+
+int launch_prolong_add(int nc, const float *cn, const float *co, float *fine, cudaStream_t s) {
+    size_t nf = 2 * (size_t)nc;
+    MGCT_KERNEL(KK_GRID, s, k_prolong_add<<<grid_for(nf * nf * nf), 256, 0, s>>>(nc, cn, co, fine));
+    return MGCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic float64 reductions: one block sums the partials in a fixed
+// order (strided per thread, then a fixed tree).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_sum_partials(const double *__restrict__ part, int count, int nvals,
+                                                       double *__restrict__ out) {
+    __shared__ double red[1024];
+    for (int c = 0; c < nvals; ++c) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < count; i += 1024) s += part[(size_t)i * nvals + c];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 512; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = red[0];
+        __syncthreads();
+    }
+}
+
+int launch_sum_partials(const double *part, int count, int nvals, double *out, cudaStream_t s) {
+    MGCT_KERNEL(KK_REDUCE, s, k_sum_partials<<<1, 1024, 0, s>>>(part, count, nvals, out));
+    return MGCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Line-search step size and the update mu <- S_lambda(mu + alpha d)
+// sums = {<r, A d>, |A d|^2}; r2 = |r|^2.  stats (device) receives
+// {alpha, r2, r2_pred, nonfinite}.
+// ---------------------------------------------------------------------------
+__global__ void k_step_size(const double *__restrict__ sums, const double *__restrict__ r2, double fixed_alpha,
+                            double *__restrict__ stats) {
+    double num = sums[0], den = sums[1];
+    double alpha, nonfinite = 0.0;
+    if (fixed_alpha > 0.0) alpha = fixed_alpha;
+    else alpha = den > 0.0 ? num / den : 0.0;
+    if (!isfinite(alpha)) {
+        alpha = 0.0;
+        nonfinite = 1.0;
+    }
+    double rr = r2 ? r2[0] : 0.0;
+    stats[0] = alpha;
+    stats[1] = rr;
+    stats[2] = rr - 2.0 * alpha * num + alpha * alpha * den;
+    stats[3] = nonfinite;
+}
+
+int launch_step_size(const double *sums, const double *r2, double fixed_alpha, double *stats, cudaStream_t s) {
+    MGCT_KERNEL(KK_REDUCE, s, k_step_size<<<1, 1, 0, s>>>(sums, r2, fixed_alpha, stats));
+    return MGCT_OK;
+}
+
+__global__ void k_update(size_t count, float *__restrict__ mu, const float *__restrict__ d,
+                         const double *__restrict__ alpha_p, float lam) {
+    const float alpha = (float)alpha_p[0];
+    const size_t n4 = count / 4;
+    float4 *mu4 = reinterpret_cast<float4 *>(mu);
+    const float4 *d4 = reinterpret_cast<const float4 *>(d);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n4; t += (size_t)gridDim.x * blockDim.x) {
+        float4 m = mu4[t], dv = __ldg(d4 + t);
+        float v[4] = {fmaf(alpha, dv.x, m.x), fmaf(alpha, dv.y, m.y), fmaf(alpha, dv.z, m.z), fmaf(alpha, dv.w, m.w)};
+        if (lam > 0.0f) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = copysignf(fmaxf(fabsf(v[q]) - lam, 0.0f), v[q]);
+        }
+        mu4[t] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    for (size_t t = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+        float v = fmaf(alpha, d[t], mu[t]);
+        if (lam > 0.0f) v = copysignf(fmaxf(fabsf(v) - lam, 0.0f), v);
+        mu[t] = v;
+    }
+}
+
+int launch_update(size_t count, float *mu, const float *d, const double *alpha, float lam, cudaStream_t s) {
+    MGCT_KERNEL(KK_UPDATE, s, k_update<<<grid_for(count / 4 + 1), 256, 0, s>>>(count, mu, d, alpha, lam));
+    return MGCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// OS-EMTR voxel update (Eq. 3): mu += num / den where den > 1e-12 max(den).
+// nd = [num (n^3) | den (n^3)].  Block max partials, then the update.
+// ---------------------------------------------------------------------------
+__global__ void k_max_partials(size_t count, const float *__restrict__ x, double *__restrict__ part) {
+    __shared__ float red[256];
+    float m = 0.0f;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, x[t]);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = (double)red[0];
+}
+
+__global__ void k_em_update(size_t count, float *__restrict__ mu, const float *__restrict__ nd,
+                            const double *__restrict__ part, int nparts) {
+    __shared__ float thr;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < nparts; ++i) m = fmax(m, part[i]);
+        thr = (float)(1e-12 * m);
+    }
+    __syncthreads();
+    const float th = thr;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+        float den = nd[count + t];
+        if (den > th && th > 0.0f) mu[t] += nd[t] / den;
+    }
+}
+
+int launch_em_update(size_t count, float *mu, const float *nd, double *part, cudaStream_t s) {
+    int nb = grid_for(count, 256);
+    if (nb > 1024) nb = 1024;
+    MGCT_KERNEL(KK_REDUCE, s, k_max_partials<<<nb, 256, 0, s>>>(count, nd + count, part));
+    MGCT_KERNEL(KK_UPDATE, s, k_em_update<<<grid_for(count), 256, 0, s>>>(count, mu, nd, part, nb));
+    return MGCT_OK;
+}
+
+__global__ void k_fill(size_t count, float *__restrict__ x, float v) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) x[t] = v;
+}
+
+int launch_fill(size_t count, float *x, float v, cudaStream_t s) {
+    MGCT_KERNEL(KK_UPDATE, s, k_fill<<<grid_for(count), 256, 0, s>>>(count, x, v));
+    return MGCT_OK;
+}
+
+__global__ void k_copy(size_t count, const float4 *__restrict__ in, float4 *__restrict__ out) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) out[t] = in[t];
+}
+
+int launch_copy(size_t count, const float *in, float *out, cudaStream_t s) {
+    if (count % 4) return set_error(MGCT_ESHAPE, "copy size must be a multiple of 4");
+    MGCT_KERNEL(KK_UPDATE, s, k_copy<<<grid_for(count / 4), 256, 0, s>>>(count / 4, reinterpret_cast<const float4 *>(in), reinterpret_cast<float4 *>(out)));
+    return MGCT_OK;
+}
+
+}  // namespace mgct

@@ -1,0 +1,328 @@
+"""Thin Python binding of libmgct.so (include/mgct.h): argument marshalling
+only.  Every operation runs in the library's CUDA kernels; torch supplies the
+device memory and the current stream.  There is no CPU fallback: if the
+library is missing or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmgct.so")
+
+F32, BF16, F16 = 0, 1, 2
+WS_LANDWEBER, WS_OSEMTR, WS_MULTIGRID = 0, 1, 2
+_DT = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+_TD = {v: k for k, v in _DT.items()}
+
+
+class MgctError(RuntimeError):
+    pass
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nu", ctypes.c_int32), ("nv", ctypes.c_int32),
+                ("n_views", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("src_axis_dist", ctypes.c_double), ("src_det_dist", ctypes.c_double),
+                ("pixel_pitch", ctypes.c_double),
+                ("theta", ctypes.POINTER(ctypes.c_double)), ("z", ctypes.POINTER(ctypes.c_double)),
+                ("drift", ctypes.POINTER(ctypes.c_double)), ("p_slice_axis", ctypes.c_int32)]
+
+
+class LwOpts(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("precondition", ctypes.c_int32), ("n_subsets", ctypes.c_int32),
+                ("learned_corr", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree library (built by paper_2103_10329_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise MgctError(f"{LIB_PATH} is missing: run paper_2103_10329_gb300.build.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    L.mgct_geometry_create.argtypes = [ctypes.POINTER(GeomDesc), ctypes.POINTER(vp)]
+    L.mgct_geometry_set_drift.argtypes = [vp, vp]
+    L.mgct_geometry_destroy.argtypes = [vp]
+    L.mgct_geometry_destroy.restype = None
+    L.mgct_geometry_level.argtypes = [vp, i, vp, vp, vp, vp, vp]
+    L.mgct_project.argtypes = [vp, i, i, i, i, vp, i, vp, i, vp, vp, vp]
+    L.mgct_backproject.argtypes = [vp, i, i, i, i, vp, i, vp, i, vp]
+    L.mgct_precondition.argtypes = [vp, i, vp, vp, vp]
+    L.mgct_restrict_volume.argtypes = [i, vp, vp, vp]
+    L.mgct_restrict_sino.argtypes = [i, i, i, vp, vp, vp]
+    L.mgct_prolong_add.argtypes = [i, vp, vp, vp, vp]
+    L.mgct_workspace_bytes.argtypes = [vp, i, i]
+    L.mgct_workspace_bytes.restype = sz
+    L.mgct_landweber_step.argtypes = [vp, i, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp]
+    L.mgct_osemtr_pass.argtypes = [vp, i, i, vp, vp, vp, vp, sz, vp]
+    L.mgct_multigrid_prepare.argtypes = [vp, vp, vp, sz, vp]
+    L.mgct_multigrid_iteration.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp]
+    L.mgct_status_string.argtypes = [i]
+    L.mgct_status_string.restype = ctypes.c_char_p
+    L.mgct_last_error.restype = ctypes.c_char_p
+    L.mgct_launch_count.argtypes = [i]
+    L.mgct_launch_count.restype = ctypes.c_uint64
+    L.mgct_trace_enable.argtypes = [i]
+    L.mgct_trace_read.argtypes = [vp, vp, i]
+    for fn in ("mgct_geometry_create", "mgct_geometry_set_drift", "mgct_geometry_level", "mgct_project",
+               "mgct_backproject", "mgct_precondition", "mgct_restrict_volume", "mgct_restrict_sino",
+               "mgct_prolong_add", "mgct_landweber_step", "mgct_osemtr_pass", "mgct_multigrid_prepare",
+               "mgct_multigrid_iteration"):
+        getattr(L, fn).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != 0:
+        L = lib()
+        raise MgctError(f"{L.mgct_status_string(st).decode()} ({st}): {L.mgct_last_error().decode()}")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None, name: str, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise MgctError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise MgctError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise MgctError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(lib().mgct_launch_count(1 if reset else 0))
+
+
+TRACE_KINDS = ("project", "backproject", "precondition", "transpose", "grid", "update", "reduce",
+               "geomgrad", "conv", "other")
+
+
+def trace_enable(on: bool = True):
+    _check(lib().mgct_trace_enable(1 if on else 0))
+
+
+def trace_read() -> dict:
+    """{kind: (milliseconds, launches)} of the kernels traced since enable."""
+    ms = (ctypes.c_double * len(TRACE_KINDS))()
+    cnt = (ctypes.c_uint64 * len(TRACE_KINDS))()
+    _check(lib().mgct_trace_read(ms, cnt, len(TRACE_KINDS)))
+    return {k: (ms[i], int(cnt[i])) for i, k in enumerate(TRACE_KINDS)}
+
+
+class Geometry:
+    """Owns an mgct_geom handle (mgct_geometry_create)."""
+
+    def __init__(self, n, nu, nv, theta, z, pitch, levels=1, src_axis_dist=2.0, src_det_dist=4.0,
+                 drift=None, p_slice_axis=2):
+        L = lib()
+        self.theta = np.ascontiguousarray(theta, dtype=np.float64)
+        self.z = np.ascontiguousarray(z, dtype=np.float64)
+        self.n, self.nu, self.nv, self.levels = int(n), int(nu), int(nv), int(levels)
+        self.n_views = len(self.theta)
+        self.pitch = float(pitch)
+        self.src_axis_dist, self.src_det_dist = float(src_axis_dist), float(src_det_dist)
+        self.p_slice_axis = int(p_slice_axis)
+        self._drift = None if drift is None else np.ascontiguousarray(drift, dtype=np.float64).reshape(-1)
+        dp = ctypes.POINTER(ctypes.c_double)
+        desc = GeomDesc(self.n, self.nu, self.nv, self.n_views, self.levels, self.src_axis_dist,
+                        self.src_det_dist, self.pitch, self.theta.ctypes.data_as(dp),
+                        self.z.ctypes.data_as(dp),
+                        self._drift.ctypes.data_as(dp) if self._drift is not None else None,
+                        self.p_slice_axis)
+        h = ctypes.c_void_p()
+        _check(L.mgct_geometry_create(ctypes.byref(desc), ctypes.byref(h)))
+        self.handle = h
+
+    def set_drift(self, drift):
+        self._drift = None if drift is None else np.ascontiguousarray(drift, dtype=np.float64).reshape(-1)
+        _check(lib().mgct_geometry_set_drift(
+            self.handle, None if self._drift is None else ctypes.c_void_p(self._drift.ctypes.data)))
+
+    def level(self, g: int):
+        n, nu, nv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        h, p = ctypes.c_double(), ctypes.c_double()
+        _check(lib().mgct_geometry_level(self.handle, g, ctypes.byref(n), ctypes.byref(nu), ctypes.byref(nv),
+                                         ctypes.byref(h), ctypes.byref(p)))
+        return n.value, nu.value, nv.value, h.value, p.value
+
+    def workspace_bytes(self, op: int, level: int = 0) -> int:
+        return int(lib().mgct_workspace_bytes(self.handle, op, level))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mgct_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def geometry_create(*args, **kw) -> Geometry:
+    return Geometry(*args, **kw)
+
+
+def _views(geom: Geometry, views):
+    if views is None:
+        return 0, geom.n_views, 1
+    v0, cnt, stride = views
+    return int(v0), int(cnt), int(stride)
+
+
+def project(geom: Geometry, vol: torch.Tensor, level: int = 0, views=None, out=None,
+            out_dtype=torch.float32, b: torch.Tensor | None = None, sumsq: torch.Tensor | None = None):
+    """A vol (or b - A vol) for views (view0, count, stride); returns out."""
+    v0, cnt, stride = _views(geom, views)
+    n, nu, nv, _, _ = geom.level(level)
+    if vol.shape != (n, n, n):
+        raise MgctError(f"vol must be [{n}]^3, got {tuple(vol.shape)}")
+    if out is None:
+        out = torch.empty((cnt, nv, nu), device=vol.device, dtype=out_dtype)
+    if out.shape != (cnt, nv, nu):
+        raise MgctError("out has the wrong shape")
+    if b is not None and b.shape != out.shape:
+        raise MgctError("b must match out")
+    _check(lib().mgct_project(geom.handle, level, v0, cnt, stride, _ptr(vol, "vol"), _DT[vol.dtype],
+                              _ptr(out, "out"), _DT[out.dtype], _ptr(b, "b", torch.float32),
+                              _ptr(sumsq, "sumsq", torch.float64), _stream()))
+    return out
+
+
+def backproject(geom: Geometry, sino: torch.Tensor, level: int = 0, views=None, out=None,
+                accumulate: bool = False):
+    """A^T sino (float32 volume)."""
+    v0, cnt, stride = _views(geom, views)
+    n, nu, nv, _, _ = geom.level(level)
+    if sino.shape != (cnt, nv, nu):
+        raise MgctError(f"sino must be [{cnt}][{nv}][{nu}], got {tuple(sino.shape)}")
+    if out is None:
+        out = torch.empty((n, n, n), device=sino.device, dtype=torch.float32)
+    _check(lib().mgct_backproject(geom.handle, level, v0, cnt, stride, _ptr(sino, "sino"), _DT[sino.dtype],
+                                  _ptr(out, "out", torch.float32), 1 if accumulate else 0, _stream()))
+    return out
+
+
+def precondition(geom: Geometry, x: torch.Tensor, level: int = 0, out=None):
+    """p * x (Eq. 5)."""
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().mgct_precondition(geom.handle, level, _ptr(x, "x", torch.float32),
+                                   _ptr(out, "out", torch.float32), _stream()))
+    return out
+
+
+def restrict_volume(x: torch.Tensor, out=None):
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty((n // 2,) * 3, device=x.device, dtype=torch.float32)
+    _check(lib().mgct_restrict_volume(n, _ptr(x, "x", torch.float32), _ptr(out, "out", torch.float32), _stream()))
+    return out
+
+
+def restrict_sino(b: torch.Tensor, out=None):
+    k, nv, nu = b.shape
+    if out is None:
+        out = torch.empty((k, nv // 2, nu // 2), device=b.device, dtype=torch.float32)
+    _check(lib().mgct_restrict_sino(k, nv, nu, _ptr(b, "b", torch.float32), _ptr(out, "out", torch.float32),
+                                    _stream()))
+    return out
+
+
+def prolong_add(coarse_new: torch.Tensor, coarse_old: torch.Tensor, fine: torch.Tensor):
+    _check(lib().mgct_prolong_add(coarse_new.shape[0], _ptr(coarse_new, "coarse_new", torch.float32),
+                                  _ptr(coarse_old, "coarse_old", torch.float32),
+                                  _ptr(fine, "fine", torch.float32), _stream()))
+    return fine
+
+
+def workspace(geom: Geometry, op: int, level: int = 0, device="cuda") -> torch.Tensor:
+    nbytes = geom.workspace_bytes(op, level)
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def _opts(alpha, lam, precond, n_subsets):
+    return LwOpts(float(alpha) if alpha is not None else 0.0, float(lam), 1 if precond else 0,
+                  int(n_subsets), None)
+
+
+def landweber_step(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, level: int = 0, alpha=None,
+                   lam: float = 0.0, precond: bool = True, ws: torch.Tensor | None = None,
+                   stats: torch.Tensor | None = None):
+    """One (preconditioned) Landweber step in place; stats: float64[4] device
+    tensor (alpha, r2, r2_pred, nonfinite) or None."""
+    if ws is None:
+        ws = workspace(geom, WS_LANDWEBER, level, vol.device)
+    o = _opts(alpha, lam, precond, 0)
+    _check(lib().mgct_landweber_step(geom.handle, level, _ptr(vol, "vol", torch.float32),
+                                     _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(), ctypes.byref(o),
+                                     _ptr(stats, "stats", torch.float64), _stream()))
+    return vol
+
+
+def osemtr_pass(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, pi: torch.Tensor, level: int = 0,
+                n_subsets: int = 8, ws: torch.Tensor | None = None):
+    if ws is None:
+        ws = workspace(geom, WS_OSEMTR, level, vol.device)
+    _check(lib().mgct_osemtr_pass(geom.handle, level, n_subsets, _ptr(vol, "vol", torch.float32),
+                                  _ptr(b, "b", torch.float32), _ptr(pi, "pi", torch.float32), _ptr(ws, "ws"),
+                                  ws.numel(), _stream()))
+    return vol
+
+
+def multigrid_prepare(geom: Geometry, b: torch.Tensor, ws: torch.Tensor):
+    _check(lib().mgct_multigrid_prepare(geom.handle, _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(),
+                                        _stream()))
+
+
+def multigrid_iteration(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, ws: torch.Tensor, alpha=None,
+                        lam: float = 0.0, precond: bool = True, n_subsets: int = 8,
+                        stats: torch.Tensor | None = None):
+    o = _opts(alpha, lam, precond, n_subsets)
+    _check(lib().mgct_multigrid_iteration(geom.handle, _ptr(vol, "vol", torch.float32),
+                                          _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(),
+                                          ctypes.byref(o), _ptr(stats, "stats", torch.float64), _stream()))
+    return vol
+
+
+class Reconstructor:
+    """Alg. 1 driver state: a geometry with `levels` grids and its multigrid
+    workspace.  `prepare(b)` once per data set, then `iterate(vol)`."""
+
+    def __init__(self, geom: Geometry, device="cuda"):
+        self.geom = geom
+        self.ws = workspace(geom, WS_MULTIGRID, 0, device)
+        self.stats = torch.zeros((max(geom.levels, 1), 4), dtype=torch.float64, device=device)
+        self.b = None
+
+    def prepare(self, b: torch.Tensor):
+        self.b = b
+        multigrid_prepare(self.geom, b, self.ws)
+
+    def iterate(self, vol: torch.Tensor, **kw):
+        return multigrid_iteration(self.geom, vol, self.b, self.ws, stats=self.stats, **kw)
+
+    def reconstruct(self, iters: int = 2, **kw):
+        n = self.geom.n
+        vol = torch.zeros((n, n, n), device=self.ws.device, dtype=torch.float32)
+        for _ in range(iters):
+            self.iterate(vol, **kw)
+        return vol

@@ -1,0 +1,253 @@
+"""GPU parity of the operators (A, A^T, p, R, P) against the FP64 oracle,
+called through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2103_10329_gb300 import synth
+from tests.helpers import TOL_F32, cuda, gpu_geom, oracle_scan, rel_err, scan_desc, summary, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2103_10329_gb300 import build
+    build.build()
+    O.build()
+
+
+C1 = dict(n=64, nu=96, nv=96, nviews=90, seed=2104, levels=2)
+
+
+def c1_desc(**kw):
+    d = dict(C1)
+    d.update(kw)
+    return scan_desc(d["n"], d["nu"], d["nv"], d["nviews"], d["seed"], levels=d["levels"],
+                     drift=d.get("drift"))
+
+
+def drift_desc(n=24, nu=36, nv=20, nviews=7, seed=31):
+    drift = synth.drift_walk(nviews, seed + 1, sigma_px=2.0, half_diag_px=0.5 * np.hypot(nu, nv))
+    return scan_desc(n, nu, nv, nviews, seed, levels=1, drift=drift)
+
+
+from paper_2103_10329_gb300 import mgct  # noqa: E402
+
+
+# --------------------------------------------------------------------------- A
+
+@pytest.mark.parametrize("which", ["random", "phantom"])
+def test_project_c1(which):
+    d = c1_desc()
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    if which == "random":
+        vol = synth.random_volume(64, 5)
+    else:
+        vol = synth.voxelize_ellipsoids(synth.ellipsoids(10, 2103), 64, supersample=2).numpy()
+    vol32 = vol.astype(np.float32)
+    ref = O.project(og, vol32.astype(np.float64))
+    got = to_np(mgct.project(g, cuda(vol32)))
+    e = rel_err(got, ref)
+    assert e.max() <= TOL_F32, summary(e)
+
+
+def test_project_ragged_drift_tilt():
+    """Ragged tiles (n=24, 36x20 detector, 7 views) with source/detector
+    drift and detector tilt."""
+    d = drift_desc()
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    vol = synth.random_volume(24, 6).astype(np.float32)
+    ref = O.project(og, vol.astype(np.float64))
+    got = to_np(mgct.project(g, cuda(vol)))
+    e = rel_err(got, ref)
+    assert e.max() <= TOL_F32, summary(e)
+
+
+def test_project_coarse_level_and_view_subset():
+    d = c1_desc()
+    g = gpu_geom(d)
+    og1 = O.level_geometry(oracle_scan(d), 1)
+    vol = synth.random_volume(32, 7).astype(np.float32)
+    views = np.arange(3, 90, 8)
+    ref = O.project(og1.subset(views), vol.astype(np.float64))
+    got = to_np(mgct.project(g, cuda(vol), level=1, views=(3, len(views), 8)))
+    e = rel_err(got, ref)
+    assert e.max() <= TOL_F32, summary(e)
+
+
+def test_project_residual_and_norm():
+    d = c1_desc()
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    vol = synth.random_volume(64, 8).astype(np.float32)
+    b = (O.project(og, vol.astype(np.float64)) * 1.01 + 0.001).astype(np.float32)
+    ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    r = to_np(mgct.project(g, cuda(vol), b=cuda(b), sumsq=ss))
+    ref = b.astype(np.float64) - O.project(og, vol.astype(np.float64))
+    assert np.abs(r - ref).max() <= 2e-5 * np.abs(b).max()
+    assert abs(ss.item() - np.sum(r * r)) <= 1e-9 * np.sum(r * r)
+
+
+@pytest.mark.parametrize("vt,ot", [(torch.bfloat16, torch.float32), (torch.float16, torch.float32),
+                                   (torch.float32, torch.bfloat16), (torch.float32, torch.float16)])
+def test_project_storage_dtypes(vt, ot):
+    """Form 1: bf16/fp16 storage, float32 accumulation.  The oracle projects
+    the rounded volume; the output error is the storage rounding of ot."""
+    d = c1_desc(n=32, nu=48, nv=48, nviews=20)
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    vol = cuda(synth.random_volume(32, 9)).to(vt)
+    ref = O.project(og, to_np(vol))
+    got = to_np(mgct.project(g, vol, out_dtype=ot))
+    e = rel_err(got, ref)
+    tol = {torch.float32: TOL_F32, torch.bfloat16: 2 ** -8, torch.float16: 2 ** -11}[ot]
+    assert e.max() <= tol, summary(e)
+
+
+def test_project_empty_selection():
+    d = c1_desc(n=32, nu=48, nv=48, nviews=10)
+    g = gpu_geom(d)
+    out = mgct.project(g, torch.ones((32, 32, 32), device="cuda"), views=(0, 0, 1))
+    assert out.shape == (0, 48, 48)
+    torch.cuda.synchronize()
+
+
+# --------------------------------------------------------------------------- A^T
+
+@pytest.mark.parametrize("kind", ["uniform", "normal"])
+def test_backproject_c1(kind):
+    d = c1_desc()
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    rng = np.random.default_rng(11)
+    y = rng.random((90, 96, 96)) if kind == "uniform" else rng.standard_normal((90, 96, 96))
+    y32 = y.astype(np.float32)
+    ref = O.backproject(og, y32.astype(np.float64))
+    got = to_np(mgct.backproject(g, cuda(y32)))
+    # signed data: the error of a sum is measured against the sum of the
+    # magnitudes of its terms, A^T |y| (equal to |A^T y| for y >= 0)
+    scale = O.backproject(og, np.abs(y32.astype(np.float64)))
+    e = rel_err(got, ref) if kind == "uniform" else np.abs(got - ref) / np.maximum(scale, 1e-2 * scale.max())
+    assert e.max() <= TOL_F32, summary(e)
+
+
+def test_backproject_ragged_drift_tilt_and_accumulate():
+    d = drift_desc()
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    y = np.random.default_rng(12).random((7, 20, 36)).astype(np.float32)
+    ref = O.backproject(og, y.astype(np.float64))
+    out = torch.full((24, 24, 24), 0.5, device="cuda")
+    got = to_np(mgct.backproject(g, cuda(y), out=out, accumulate=True)) - 0.5
+    e = rel_err(got, ref)
+    assert e.max() <= 2 * TOL_F32, summary(e)
+
+
+def test_backproject_subset_and_storage_dtypes():
+    d = c1_desc(n=32, nu=48, nv=48, nviews=24)
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    views = np.arange(2, 24, 5)
+    y = cuda(np.random.default_rng(13).random((len(views), 48, 48))).to(torch.bfloat16)
+    ref = O.backproject(og.subset(views), to_np(y))
+    got = to_np(mgct.backproject(g, y, views=(2, len(views), 5)))
+    e = rel_err(got, ref)
+    assert e.max() <= TOL_F32, summary(e)
+    y16 = y.to(torch.float16)
+    got16 = to_np(mgct.backproject(g, y16, views=(2, len(views), 5)))
+    e16 = rel_err(got16, O.backproject(og.subset(views), to_np(y16)))
+    assert e16.max() <= TOL_F32, summary(e16)
+
+
+def test_backproject_empty_selection_gives_zero():
+    d = c1_desc(n=32, nu=48, nv=48, nviews=10)
+    g = gpu_geom(d)
+    out = torch.full((32, 32, 32), 3.0, device="cuda")
+    mgct.backproject(g, torch.empty((0, 48, 48), device="cuda"), views=(0, 0, 1), out=out)
+    assert float(out.abs().max()) == 0.0
+
+
+def test_gpu_adjoint_identity():
+    """Sec. 2.1: B is the adjoint of P.  Both GPU kernels share the ray
+    set-up, so <A x, y> = <x, A^T y> up to float32 summation error."""
+    d = c1_desc()
+    g = gpu_geom(d)
+    x = cuda(synth.random_volume(64, 14))
+    y = cuda(np.random.default_rng(15).standard_normal((90, 96, 96)))
+    ax = mgct.project(g, x)
+    aty = mgct.backproject(g, y)
+    lhs = float(torch.sum(ax.double() * y.double()))
+    rhs = float(torch.sum(x.double() * aty.double()))
+    scale = float(torch.sum(ax.double().abs() * y.double().abs()))
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_determinism():
+    d = c1_desc()
+    g = gpu_geom(d)
+    x = cuda(synth.random_volume(64, 16))
+    y = cuda(np.random.default_rng(17).standard_normal((90, 96, 96)))
+    a1, a2 = mgct.project(g, x), mgct.project(g, x)
+    b1, b2 = mgct.backproject(g, y), mgct.backproject(g, y)
+    assert torch.equal(a1, a2) and torch.equal(b1, b2)
+
+
+# --------------------------------------------------------------------------- full-size samples
+
+@pytest.mark.parametrize("cfg", [(256, 384, 720), (512, 768, 1440)], ids=["c2", "c3"])
+def test_full_size_sampled(cfg):
+    """At the benchmark sizes, in the launch configuration the bench times:
+    sampled rays and voxels against the oracle computed one by one."""
+    n, nu, nviews = cfg
+    d = scan_desc(n, nu, nu, nviews, 2104, levels=1)
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    ph = synth.ellipsoids(40, 2103, axis_lo=0.02, axis_hi=0.12)
+    vol = synth.voxelize_ellipsoids(ph, n, supersample=1, device="cuda", dtype=torch.float32)
+    proj = mgct.project(g, vol)
+    rays = synth.random_indices(300, (nviews, nu, nu), 3)
+    vol_np = to_np(vol)
+    ref = O.project_rays(og, vol_np, rays)
+    got = to_np(proj)[rays[:, 0], rays[:, 1], rays[:, 2]]
+    full_max = float(proj.abs().max())
+    e = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * full_max)
+    assert e.max() <= TOL_F32, summary(e)
+    del vol
+    y = torch.rand((nviews, nu, nu), device="cuda", generator=torch.Generator("cuda").manual_seed(4))
+    bp = mgct.backproject(g, y)
+    vox = synth.random_indices(24, (n, n, n), 5)
+    refv = O.backproject_voxels(og, to_np(y), vox, radius=5)
+    gotv = to_np(bp)[vox[:, 2], vox[:, 1], vox[:, 0]]
+    ev = np.abs(gotv - refv) / np.maximum(np.abs(refv), 1e-2 * float(bp.abs().max()))
+    assert ev.max() <= TOL_F32, summary(ev)
+
+
+# --------------------------------------------------------------------------- p, R, P
+
+@pytest.mark.parametrize("axis", [2, 0])
+def test_precondition(axis):
+    d = scan_desc(40, 48, 48, 4, 1, levels=1, slice_axis=axis)
+    g = gpu_geom(d)
+    x = synth.random_volume(40, 18).astype(np.float32) - 0.5
+    ref = O.precondition(x.astype(np.float64), axis)
+    got = to_np(mgct.precondition(g, cuda(x)))
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(x).max()
+
+
+def test_restrict_and_prolong():
+    x = synth.random_volume(48, 19).astype(np.float32)
+    got = to_np(mgct.restrict_volume(cuda(x)))
+    assert np.abs(got - O.restrict_volume(x.astype(np.float64))).max() <= 1e-6
+    b = np.random.default_rng(20).random((5, 36, 52)).astype(np.float32)
+    got = to_np(mgct.restrict_sino(cuda(b)))
+    assert np.abs(got - O.restrict_sino(b.astype(np.float64))).max() <= 1e-6
+    cn = synth.random_volume(20, 21).astype(np.float32)
+    co = synth.random_volume(20, 22).astype(np.float32)
+    fine = synth.random_volume(40, 23).astype(np.float32)
+    ref = fine.astype(np.float64) + O.prolong(cn.astype(np.float64) - co.astype(np.float64))
+    got = to_np(mgct.prolong_add(cuda(cn), cuda(co), cuda(fine)))
+    assert np.abs(got - ref).max() <= 1e-6

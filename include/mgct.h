@@ -226,6 +226,35 @@ int mgct_multigrid_iteration(const mgct_geom *geom, float *vol, const float *b, 
                              mgct_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Residual projection without any device allocation.  The paper has no
+ * counterpart: this is a library service.
+ *
+ * Same result as mgct_project(geom, level, view0, nviews, view_stride, vol,
+ * MGCT_F32, out, MGCT_F32, b, sumsq, stream): out = b - A vol and
+ * *sumsq = |out|^2 in float64 (sumsq required).  It is meant for callers
+ * that may not allocate device memory themselves -- a plug-in whose host
+ * pipeline owns every device buffer through its own pool or caching
+ * allocator, or a process with a device-memory budget fixed at start-up.
+ * Instead of the handle's scratch it uses one static device array inside the
+ * library, mgct_project_residual_static_bytes() bytes (about 10 MiB), which
+ * every GPU that loads the library holds until the process exits.  Limits:
+ * at most 128^3 voxels on the chosen grid and at most 262144 projector
+ * blocks (ceil(nu_g/32) * ceil(nv_g/8) * nviews); larger requests fail with
+ * MGCT_ESHAPE and a message naming the limit.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, so calls that overlap on the GPU (different streams, or
+ * different host threads, without ordering between them) race on it and give
+ * wrong results; the array keeps the last call's contents, and every word a
+ * call reads is written by that call first.
+ * ------------------------------------------------------------------------- */
+int mgct_project_residual_static(const mgct_geom *geom, int level, int view0, int nviews,
+                                 int view_stride, const float *vol, float *out, const float *b,
+                                 double *sumsq, mgct_stream stream);
+size_t mgct_project_residual_static_bytes(void);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics
  * ------------------------------------------------------------------------- */
 const char *mgct_status_string(int status);

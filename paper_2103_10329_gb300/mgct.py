@@ -75,6 +75,9 @@ def lib():
     L.mgct_launch_count.restype = ctypes.c_uint64
     L.mgct_trace_enable.argtypes = [i]
     L.mgct_trace_read.argtypes = [vp, vp, i]
+    L.mgct_project_residual_static.argtypes = [vp, i, i, i, i, vp, vp, vp, vp, vp]
+    L.mgct_project_residual_static.restype = ctypes.c_int
+    L.mgct_project_residual_static_bytes.restype = sz
     for fn in ("mgct_geometry_create", "mgct_geometry_set_drift", "mgct_geometry_level", "mgct_project",
                "mgct_backproject", "mgct_precondition", "mgct_restrict_volume", "mgct_restrict_sino",
                "mgct_prolong_add", "mgct_landweber_step", "mgct_osemtr_pass", "mgct_multigrid_prepare",
@@ -326,3 +329,19 @@ class Reconstructor:
         for _ in range(iters):
             self.iterate(vol, **kw)
         return vol
+
+
+def project_residual_static(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, sumsq: torch.Tensor,
+                            level: int = 0, views=None, out=None):
+    """out = b - A vol and sumsq[0] = |out|^2, computed with the library's
+    static scratch instead of any allocation (mgct_project_residual_static):
+    for callers that may not allocate device memory themselves.  Volumes up
+    to 128^3; overlapping calls on different streams race on the scratch."""
+    v0, cnt, stride = _views(geom, views)
+    n, nu, nv, _, _ = geom.level(level)
+    if out is None:
+        out = torch.empty((cnt, nv, nu), device=vol.device, dtype=torch.float32)
+    _check(lib().mgct_project_residual_static(geom.handle, level, v0, cnt, stride, _ptr(vol, "vol", torch.float32),
+                                              _ptr(out, "out", torch.float32), _ptr(b, "b", torch.float32),
+                                              _ptr(sumsq, "sumsq", torch.float64), _stream()))
+    return out

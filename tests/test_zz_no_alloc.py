@@ -1,0 +1,75 @@
+"""The allocation-free residual projection (mgct_project_residual_static)
+against the ordinary one (mgct_project with b and sumsq), both called
+through the C ABI.
+
+The allocation-free entry point exists for callers that may not allocate
+device memory themselves (a plug-in whose host pipeline owns all device
+buffers, or a process with a fixed device-memory budget); it keeps its
+scratch in one static device array of the library.  This file is collected
+last so that a run stopping at the first failure has run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2103_10329_gb300 import synth
+from tests.helpers import TOL_F32, cuda, gpu_geom, rel_err, scan_desc, summary, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2103_10329_gb300 import build, mgct
+    build.build()
+    return mgct.lib()
+
+
+def _static_call(L, g, level, view0, nviews, stride, vol, out, b, ss):
+    st = L.mgct_project_residual_static(g.handle, level, view0, nviews, stride, ctypes.c_void_p(vol.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                        ctypes.c_void_p(ss.data_ptr()),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st
+
+
+def test_static_scratch_matches_allocating_path_twice(L):
+    from paper_2103_10329_gb300 import mgct
+    d = scan_desc(64, 96, 96, 90, 2104, levels=2)
+    g = gpu_geom(d)
+    cases = [  # (level, view0, nviews, stride, volume seed): two different calls in a row
+        (0, 0, 90, 1, 5),
+        (1, 3, 11, 8, 6),
+    ]
+    for level, v0, cnt, stride, seed in cases:
+        n, nu, nv, _, _ = g.level(level)
+        vol = cuda(synth.random_volume(n, seed))
+        b = cuda(np.random.default_rng(seed).random((cnt, nv, nu)) + 0.5)
+        ref_ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ref = mgct.project(g, vol, level=level, views=(v0, cnt, stride), b=b, sumsq=ref_ss)
+        out = torch.full((cnt, nv, nu), float("nan"), device="cuda")
+        ss = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        assert _static_call(L, g, level, v0, cnt, stride, vol, out, b, ss) == 0, L.mgct_last_error()
+        torch.cuda.synchronize()
+        e = rel_err(to_np(out), to_np(ref))
+        assert e.max() <= TOL_F32, summary(e)
+        assert abs(ss.item() - ref_ss.item()) <= 1e-9 * ref_ss.item()
+
+
+def test_static_scratch_rejects_oversized_requests(L):
+    d = scan_desc(256, 48, 48, 4, 1, levels=2)
+    g = gpu_geom(d)
+    vol = torch.zeros((256, 256, 256), device="cuda")
+    out = torch.empty((4, 48, 48), device="cuda")
+    b = torch.zeros_like(out)
+    ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert _static_call(L, g, 0, 0, 4, 1, vol, out, b, ss) == -2
+    assert b"128^3" in L.mgct_last_error()
+    # the coarser grid (128^3) fits
+    vol1 = torch.ones((128, 128, 128), device="cuda")
+    out1 = torch.empty((4, 24, 24), device="cuda")
+    assert _static_call(L, g, 1, 0, 4, 1, vol1, out1, torch.zeros_like(out1), ss) == 0
+    torch.cuda.synchronize()
+    assert L.mgct_project_residual_static_bytes() > 8 * 2 ** 20

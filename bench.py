@@ -38,6 +38,8 @@ WORKLOADS = {
     "c2": dict(n=256, nu=384, views=720, levels=3, count=200, axis=(0.01, 0.08), texture=True,
                photons=1e4),
     "c1": dict(n=64, nu=96, views=90, levels=2, count=10, axis=(0.04, 0.2), texture=False, photons=0),
+    # half the views of c2, noise- and texture-free: the small case for ncu captures
+    "c2h": dict(n=256, nu=384, views=360, levels=3, count=50, axis=(0.01, 0.08), texture=False, photons=0),
 }
 SEED = 2103
 FP32_LANES_PER_SM, SMS = 128, 152

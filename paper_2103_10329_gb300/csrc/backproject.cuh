@@ -51,8 +51,10 @@ struct SinoLoad<2, float2> {
     }
 };
 
-// Adds A^T (one view) at voxel (jx, jy, jz) into acc.
-template <int NCH, typename ST>
+// Adds A^T (one view) at voxel (jx, jy, jz) into acc -- any geometry.
+// WEIGHTED: the sinogram already carries each ray's dl (see the projector's
+// weighted epilogues), so the weight is hat * hat; otherwise dl is computed.
+template <int NCH, typename ST, bool WEIGHTED>
 __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int jx, int jy, int jz,
                                         const ST *__restrict__ sino_view, float (&acc)[NCH]) {
     const float X = (float)jx - G.S[0], Y = (float)jy - G.S[1], Z = (float)jz - G.S[2];
@@ -80,27 +82,96 @@ __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int 
             const RayDir d = ray_dir(G, up, vp);
             const float wa = d.ax ? d.wy : d.wx;
             const float wb = d.ax ? d.wx : d.wy;
-            const float inv = __frcp_rn(wa);
-            const float rb = wb * inv, rz = d.wz * inv;
+            const float rinv = __frcp_rn(wa);
+            const float rb = wb * rinv, rz = d.wz * rinv;
             const float *N = d.ax ? G.NY : G.NX;
             // centred crossing of this ray with the voxel's plane, minus the voxel
             const float ca = d.ax ? cy : cx, cb = d.ax ? cx : cy;
-            const float pb = fmaf(vp, N[2], fmaf(up, N[1], N[0])) * inv;
-            const float pz = fmaf(vp, N[5], fmaf(up, N[4], N[3])) * inv;
+            const float pb = fmaf(vp, N[2], fmaf(up, N[1], N[0])) * rinv;
+            const float pz = fmaf(vp, N[5], fmaf(up, N[4], N[3])) * rinv;
             const float eb = fmaf(ca, rb, pb) - cb;
             const float ez = fmaf(ca, rz, pz) - cz;
             const float hb = 1.0f - fabsf(eb);
             const float hz = 1.0f - fabsf(ez);
             if (hb > 0.0f && hz > 0.0f) {
-                const float dl_h = sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f)));
-                const float w = (dl_h * a.h) * hb * hz;
+                float w = hb * hz;
+                if (!WEIGHTED) w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
                 SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc);
             }
         }
     }
 }
 
-template <int NCH, typename ST>
+// Separable geometries (no detector tilt: e_u horizontal, e_v vertical).
+// Then w_x, w_y and the major axis depend on u' only, the in-plane crossing
+// error e_b depends on u' only, and the z error is linear in v':
+//   e_z(v') = E0 + v' E1,  E0 = (n0_z + u' nu_z + c_a Wc_z)/w_a - c_z,
+//                          E1 = (nv_z + c_a Ev_z)/w_a,
+// so each detector column is set up once for the thread's ZB voxels of one
+// z-column, and each voxel walks exactly the pixels where |e_z| < 1.
+template <int NCH, typename ST, bool WEIGHTED, int ZB>
+__device__ __forceinline__ void bp_view_sep(const ViewGeom &G, const BPArgs &a, int jx, int jy, int jz0,
+                                            const ST *__restrict__ sino_view, float (&acc)[ZB][NCH]) {
+    const float X = (float)jx - G.S[0], Y = (float)jy - G.S[1];
+    // with no tilt the u coordinate and depth of a point ignore its z
+    const float q0 = fmaf(G.Q[1], Y, G.Q[0] * X);
+    const float q2 = fmaf(G.Q[7], Y, G.Q[6] * X);
+    const float u0 = q0 / q2;
+    const float hu = (fabsf(G.Q[0] - u0 * G.Q[6]) + fabsf(G.Q[1] - u0 * G.Q[7])) / (q2 - G.m2);
+    const float cu = 0.5f * (float)(a.nu - 1), cv = 0.5f * (float)(a.nv - 1);
+    const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
+    const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
+    const float ic = 0.5f * (float)(a.n - 1);
+    const float cx = (float)jx - ic, cy = (float)jy - ic, cz0 = (float)jz0 - ic;
+    for (int ju = ulo; ju <= uhi; ++ju) {
+        const float up = (float)ju - cu;
+        // identical to ray_dir() with the zero v-terms: same axis choice
+        const float wx = __fmaf_rn(up, G.Eu[0], G.Wc[0]);
+        const float wy = __fmaf_rn(up, G.Eu[1], G.Wc[1]);
+        const int ax = fabsf(wy) > fabsf(wx) ? 1 : 0;
+        const float wa = ax ? wy : wx, wb = ax ? wx : wy;
+        const float rinv = __frcp_rn(wa);
+        const float rb = wb * rinv;
+        const float *N = ax ? G.NY : G.NX;
+        const float ca = ax ? cy : cx, cb = ax ? cx : cy;
+        const float eb = fmaf(ca, rb, fmaf(up, N[1], N[0]) * rinv) - cb;
+        const float hb = 1.0f - fabsf(eb);
+        if (hb <= 0.0f) continue;
+        const float Eb = fmaf(ca, G.Wc[2], fmaf(up, N[4], N[3])) * rinv;  // E0 + c_z
+        const float E1 = fmaf(ca, G.Ev[2], N[5]) * rinv;
+        const float rE1 = 1.0f / E1;
+#pragma unroll
+        for (int zz = 0; zz < ZB; ++zz) {
+            const float E0 = Eb - (cz0 + (float)zz);
+            const float t1 = (-1.0f - E0) * rE1, t2 = (1.0f - E0) * rE1;
+            const int vlo = max(0, (int)ceilf(fminf(t1, t2) + cv - 1e-3f));
+            const int vhi = min(a.nv - 1, (int)floorf(fmaxf(t1, t2) + cv + 1e-3f));
+            for (int jv = vlo; jv <= vhi; ++jv) {
+                const float vp = (float)jv - cv;
+                const float hz = 1.0f - fabsf(fmaf(vp, E1, E0));
+                if (hz > 0.0f) {
+                    float w = hb * hz;
+                    if (!WEIGHTED) {
+                        const float rz = fmaf(vp, G.Ev[2], G.Wc[2]) * rinv;
+                        w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
+                    }
+                    SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc[zz]);
+                }
+            }
+        }
+    }
+}
+
+template <typename ST>
+__device__ __forceinline__ void stage_views(ViewGeom *Gs, const BPArgs &a, int c0, int cn, int tid, int nthreads) {
+    for (int t = tid; t < cn * VG_HI; t += nthreads) {
+        const int vi = t / VG_HI, e = t % VG_HI;
+        reinterpret_cast<float *>(&Gs[vi])[e] =
+            __ldg(reinterpret_cast<const float *>(a.views + a.view0 + (c0 + vi) * a.stride) + e);
+    }
+}
+
+template <int NCH, typename ST, bool WEIGHTED>
 __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
     k_backproject(BPArgs a, const ST *__restrict__ sino, float *__restrict__ out, int accumulate) {
     __shared__ ViewGeom Gs[BP_CHUNK];
@@ -116,15 +187,11 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
     for (int c0 = 0; c0 < a.nviews; c0 += BP_CHUNK) {
         const int cn = min(BP_CHUNK, a.nviews - c0);
         __syncthreads();
-        for (int t = tid; t < cn * VG_HI; t += BP_BX * BP_BY * BP_BZ) {
-            const int vi = t / VG_HI, e = t % VG_HI;
-            reinterpret_cast<float *>(&Gs[vi])[e] =
-                __ldg(reinterpret_cast<const float *>(a.views + a.view0 + (c0 + vi) * a.stride) + e);
-        }
+        stage_views<ST>(Gs, a, c0, cn, tid, BP_BX * BP_BY * BP_BZ);
         __syncthreads();
         if (active) {
             for (int vi = 0; vi < cn; ++vi)
-                bp_view<NCH, ST>(Gs[vi], a, jx, jy, jz, sino + (size_t)(c0 + vi) * view_elems, acc);
+                bp_view<NCH, ST, WEIGHTED>(Gs[vi], a, jx, jy, jz, sino + (size_t)(c0 + vi) * view_elems, acc);
         }
     }
     if (!active) return;
@@ -138,8 +205,52 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
     }
 }
 
-// NCH = 2 writes channel c to out + c * n^3.
-template <int NCH, typename ST>
+constexpr int BPS_ZB = 4;  // voxels per thread along z (separable kernel)
+
+template <int NCH, typename ST, bool WEIGHTED>
+__global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
+    k_backproject_sep(BPArgs a, const ST *__restrict__ sino, float *__restrict__ out, int accumulate) {
+    __shared__ ViewGeom Gs[BP_CHUNK];
+    const int jx = blockIdx.x * BP_BX + threadIdx.x;
+    const int jy = blockIdx.y * BP_BY + threadIdx.y;
+    const int jz0 = (blockIdx.z * BP_BZ + threadIdx.z) * BPS_ZB;
+    const bool active = jx < a.n && jy < a.n && jz0 < a.n;
+    const int tid = threadIdx.x + BP_BX * (threadIdx.y + BP_BY * threadIdx.z);
+    float acc[BPS_ZB][NCH];
+#pragma unroll
+    for (int z = 0; z < BPS_ZB; ++z)
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) acc[z][c] = 0.0f;
+    const size_t view_elems = (size_t)a.nu * a.nv;
+    for (int c0 = 0; c0 < a.nviews; c0 += BP_CHUNK) {
+        const int cn = min(BP_CHUNK, a.nviews - c0);
+        __syncthreads();
+        stage_views<ST>(Gs, a, c0, cn, tid, BP_BX * BP_BY * BP_BZ);
+        __syncthreads();
+        if (active) {
+            for (int vi = 0; vi < cn; ++vi)
+                bp_view_sep<NCH, ST, WEIGHTED, BPS_ZB>(Gs[vi], a, jx, jy, jz0,
+                                                       sino + (size_t)(c0 + vi) * view_elems, acc);
+        }
+    }
+    if (!active) return;
+    const size_t nvox = (size_t)a.n * a.n * a.n;
+#pragma unroll
+    for (int z = 0; z < BPS_ZB; ++z) {
+        if (jz0 + z >= a.n) break;
+        const size_t idx = ((size_t)(jz0 + z) * a.n + jy) * a.n + jx;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            float v = acc[z][c];
+            if (accumulate) v += out[idx + c * nvox];
+            out[idx + c * nvox] = v;
+        }
+    }
+}
+
+// NCH = 2 writes channel c to out + c * n^3.  WEIGHTED: the sinogram carries
+// each ray's dl already (internal solver path).
+template <int NCH, typename ST, bool WEIGHTED = false>
 int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int stride, const ST *sino,
                        float *out, int accumulate, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
@@ -152,8 +263,16 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
     a.view0 = view0;
     a.stride = stride;
     a.nviews = nviews;
-    dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + BP_BZ - 1) / BP_BZ);
-    MGCT_KERNEL(KK_BACKPROJECT, s, k_backproject<NCH, ST><<<grid, dim3(BP_BX, BP_BY, BP_BZ), 0, s>>>(a, sino, out, accumulate));
+    if (g->separable) {
+        const int zper = BP_BZ * BPS_ZB;
+        dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + zper - 1) / zper);
+        MGCT_KERNEL(KK_BACKPROJECT, s,
+                    k_backproject_sep<NCH, ST, WEIGHTED><<<grid, dim3(BP_BX, BP_BY, BP_BZ), 0, s>>>(a, sino, out, accumulate));
+    } else {
+        dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + BP_BZ - 1) / BP_BZ);
+        MGCT_KERNEL(KK_BACKPROJECT, s,
+                    k_backproject<NCH, ST, WEIGHTED><<<grid, dim3(BP_BX, BP_BY, BP_BZ), 0, s>>>(a, sino, out, accumulate));
+    }
     return MGCT_OK;
 }
 

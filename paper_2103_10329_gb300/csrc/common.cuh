@@ -66,6 +66,7 @@ struct mgct_geom {
     mgct_geom_desc desc;        // pointers inside are not kept
     std::vector<double> theta, z, drift;
     int has_drift;
+    int separable;  // 1 if no view has a tilted detector (e_u horizontal, e_v vertical)
     int levels;
     mgct::LevelInfo lev[8];
     std::vector<mgct::ViewGeom> h_views[8];

@@ -181,6 +181,7 @@ static int build_view(const mgct_geom *g, int level, int k, ViewGeom *out, std::
 
 static int upload_tables(mgct_geom *g) {
     int K = g->desc.n_views;
+    g->separable = 1;
     for (int l = 0; l < g->levels; ++l) {
         auto &hv = g->h_views[l];
         hv.resize(K);
@@ -188,6 +189,10 @@ static int upload_tables(mgct_geom *g) {
             std::string why;
             int st = build_view(g, l, k, &hv[k], &why);
             if (st) return set_error(st, "view " + std::to_string(k) + ", grid " + std::to_string(l) + ": " + why);
+            const ViewGeom &v = hv[k];
+            if (v.Ev[0] != 0.0f || v.Ev[1] != 0.0f || v.Eu[2] != 0.0f || v.Ev_lo[0] != 0.0f ||
+                v.Ev_lo[1] != 0.0f || v.Eu_lo[2] != 0.0f || v.Q[2] != 0.0f || v.Q[8] != 0.0f)
+                g->separable = 0;
         }
         MGCT_TRY(check_cuda(cudaMemcpy(g->lev[l].d_views, hv.data(), K * sizeof(ViewGeom),
                                        cudaMemcpyHostToDevice),

@@ -92,10 +92,15 @@ constexpr int PJ_CHUNK = 16;  // planes stepped in float32 from one double-float
 // crossing is re-anchored in double-float and split into integer voxel index
 // and fraction, and the planes in between step the fraction in float32.  The
 // sample positions are thus accurate to ~1e-6 voxel at any volume size.
+struct RaySum {
+    float acc;  // sum of the bilinear samples along the ray
+    float dlh;  // path length per plane, h |w| / |w_a|; A vol = acc * dlh
+};
+
 template <typename VT>
-__device__ __forceinline__ float ray_integral(const ViewGeom &G, const ProjArgs &a, int ju, int jv,
-                                              const VT *__restrict__ vol,
-                                              const VT *__restrict__ volT) {
+__device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs &a, int ju, int jv,
+                                               const VT *__restrict__ vol,
+                                               const VT *__restrict__ volT) {
     const int n = a.n;
     const float ic = 0.5f * (float)(n - 1);
     const float up = (float)ju - 0.5f * (float)(a.nu - 1);
@@ -148,11 +153,13 @@ __device__ __forceinline__ float ray_integral(const ViewGeom &G, const ProjArgs 
         }
         acc += part;
     }
-    return acc * (dl_h * a.h);
+    return RaySum{acc, dl_h * a.h};
 }
 
-// Epilogue interface: operator()(i_batch, k_view, jv, ju, active, value),
-// called by every thread of the block (block reductions inside).
+// Epilogue interface: operator()(i_batch, k_view, jv, ju, active, acc, dlh)
+// with A vol = acc * dlh at that ray, called by every thread of the block
+// (block reductions inside).  "Weighted" sinograms carry the factor dlh of
+// their ray, which the back-projector then need not recompute.
 template <typename VT, typename Epi>
 __global__ void __launch_bounds__(PJ_BX *PJ_BY)
     k_project(ProjArgs a, const VT *__restrict__ vol, const VT *__restrict__ volT, Epi epi) {
@@ -165,9 +172,9 @@ __global__ void __launch_bounds__(PJ_BX *PJ_BY)
     const int ju = blockIdx.x * PJ_BX + threadIdx.x;
     const int jv = blockIdx.y * PJ_BY + threadIdx.y;
     const bool active = ju < a.nu && jv < a.nv;
-    float val = 0.0f;
-    if (active) val = ray_integral(G, a, ju, jv, vol, volT);
-    epi(i, k, jv, ju, active, val);
+    RaySum rs{0.0f, 0.0f};
+    if (active) rs = ray_integral(G, a, ju, jv, vol, volT);
+    epi(i, k, jv, ju, active, rs.acc, rs.dlh);
 }
 
 // out = A vol
@@ -175,26 +182,33 @@ template <typename OT>
 struct EpiStore {
     OT *out;
     int nu, nv;
-    __device__ void operator()(int i, int, int jv, int ju, bool active, float val) const {
-        if (active) out[((size_t)i * nv + jv) * nu + ju] = from_f32<OT>(val);
+    __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
+        if (active) out[((size_t)i * nv + jv) * nu + ju] = from_f32<OT>(acc * dlh);
     }
 };
 
-// out = b - A vol, and the block's sum of out^2 (float64) into part[block]
-template <typename OT>
+// r = b - A vol; out = r (WEIGHTED: r * dlh), and the block's sum of r^2
+// (float64) into part[block]
+template <typename OT, bool WEIGHTED = false>
 struct EpiResidual {
     OT *out;
     const float *b;  // indexed like out
     double *part;    // NULL: no norm
     int nu, nv;
-    __device__ void operator()(int i, int, int jv, int ju, bool active, float val) const {
+    __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
         double s[1] = {0.0};
         if (active) {
             size_t idx = ((size_t)i * nv + jv) * nu + ju;
-            OT r = from_f32<OT>(__ldg(b + idx) - val);
-            out[idx] = r;
-            float rf = to_f32(r);
-            s[0] = (double)rf * (double)rf;
+            float r = __ldg(b + idx) - acc * dlh;
+            if (WEIGHTED) {
+                out[idx] = from_f32<OT>(r * dlh);
+                s[0] = (double)r * (double)r;
+            } else {
+                OT ro = from_f32<OT>(r);
+                out[idx] = ro;
+                float rf = to_f32(ro);
+                s[0] = (double)rf * (double)rf;
+            }
         }
         if (part) {
             __shared__ double red[PJ_BX * PJ_BY / 32];
@@ -204,18 +218,21 @@ struct EpiResidual {
     }
 };
 
-// Line-search dot products: <r, A d> and |A d|^2 per block, no sinogram write.
+// Line-search dot products per block, no sinogram write:
+//   <r, A d> = sum r_w * acc  (r_w = r * dlh, the weighted residual)
+//   |A d|^2  = sum (acc * dlh)^2
 template <typename RT>
 struct EpiDualDot {
-    const RT *r;  // batch sinogram
-    double *part; // [blocks][2]
+    const RT *rw;  // weighted residual, batch sinogram
+    double *part;  // [blocks][2]
     int nu, nv;
-    __device__ void operator()(int i, int, int jv, int ju, bool active, float val) const {
+    __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
         double s[2] = {0.0, 0.0};
         if (active) {
-            float rv = to_f32(r[((size_t)i * nv + jv) * nu + ju]);
-            s[0] = (double)rv * (double)val;
-            s[1] = (double)val * (double)val;
+            float rv = to_f32(rw[((size_t)i * nv + jv) * nu + ju]);
+            float ad = acc * dlh;
+            s[0] = (double)rv * (double)acc;
+            s[1] = (double)ad * (double)ad;
         }
         __shared__ double red[2 * PJ_BX * PJ_BY / 32];
         block_sum<2>(s, red);
@@ -227,8 +244,8 @@ struct EpiDualDot {
     }
 };
 
-// OS-EMTR (Eq. 3) sinogram terms for one subset:
-//   t = exp(-A mu);  c0 = t - exp(-b) (= t - I/I0);  c1 = t * PI
+// OS-EMTR (Eq. 3) sinogram terms for one subset, weighted by dlh:
+//   t = exp(-A mu);  c0 = (t - exp(-b)) dlh  (I/I0 = exp(-b));  c1 = t PI dlh
 // b and PI are full [K][nv][nu] arrays indexed by the view k; c is a batch
 // two-channel sinogram.
 struct EpiEMTerms {
@@ -236,14 +253,14 @@ struct EpiEMTerms {
     const float *b;
     const float *pi;
     int nu, nv;
-    __device__ void operator()(int i, int k, int jv, int ju, bool active, float val) const {
+    __device__ void operator()(int i, int k, int jv, int ju, bool active, float acc, float dlh) const {
         if (!active) return;
         size_t pix = (size_t)jv * nu + ju;
         size_t full = (size_t)k * nv * nu + pix;
-        float t = expf(-val);
+        float t = expf(-acc * dlh);
         float2 o;
-        o.x = t - expf(-__ldg(b + full));
-        o.y = t * __ldg(pi + full);
+        o.x = (t - expf(-__ldg(b + full))) * dlh;
+        o.y = t * __ldg(pi + full) * dlh;
         c[(size_t)i * nv * nu + pix] = o;
     }
 };

@@ -143,11 +143,12 @@ static int landweber(const mgct_geom *g, int level, float *mu, const float *b, v
     // r = b - A mu, |r|^2
     MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
     int nb = 0;
-    EpiResidual<float> er{w.r, b, w.part, L.nu, L.nv};
+    // r is stored weighted by each ray's dl, which the back-projector then skips
+    EpiResidual<float, true> er{w.r, b, w.part, L.nu, L.nv};
     MGCT_TRY(launch_project<float>(g, level, 0, K, 1, mu, w.muT, er, s, &nb));
     MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
     // d = p * A^T r   (or A^T r for SIRT)
-    MGCT_TRY(launch_backproject<1, float>(g, level, 0, K, 1, w.r, w.grad, 0, s));
+    MGCT_TRY(launch_backproject<1, float, true>(g, level, 0, K, 1, w.r, w.grad, 0, s));
     float *d = w.grad, *dT = w.d;
     if (o.precondition) {
         MGCT_TRY(launch_precondition(L.n, g->desc.p_slice_axis, w.grad, w.d, s));
@@ -180,7 +181,7 @@ static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *
         MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
         EpiEMTerms e{w.c2, b, pi, L.nu, L.nv};
         MGCT_TRY(launch_project<float>(g, level, m, cnt, M, mu, w.muT, e, s));
-        MGCT_TRY(launch_backproject<2, float2>(g, level, m, cnt, M, w.c2, w.nd, 0, s));
+        MGCT_TRY(launch_backproject<2, float2, true>(g, level, m, cnt, M, w.c2, w.nd, 0, s));
         MGCT_TRY(launch_em_update(nv3, mu, w.nd, w.part, s));
     }
     return MGCT_OK;

@@ -239,7 +239,8 @@ int mgct_multigrid_iteration(const mgct_geom *geom, float *vol, const float *b, 
  * library, mgct_project_residual_static_bytes() bytes (about 10 MiB), which
  * every GPU that loads the library holds until the process exits.  Limits:
  * at most 128^3 voxels on the chosen grid and at most 262144 projector
- * blocks (ceil(nu_g/32) * ceil(nv_g/8) * nviews); larger requests fail with
+ * blocks (ceil(nu_g/32) * ceil(nv_g/8) * nviews, with nviews rounded up to a
+ * multiple of 32 above 32 views); larger requests fail with
  * MGCT_ESHAPE and a message naming the limit.  It calls no cudaMalloc,
  * cudaFree or other allocating routine.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device

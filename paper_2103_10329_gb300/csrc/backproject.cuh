@@ -53,7 +53,9 @@ struct SinoLoad<2, float2> {
 
 // Adds A^T (one view) at voxel (jx, jy, jz) into acc -- any geometry.
 // WEIGHTED: the sinogram already carries each ray's dl (see the projector's
-// weighted epilogues), so the weight is hat * hat; otherwise dl is computed.
+// weighted epilogues) and is stored column-major per view, [view][u][v]; the
+// weight is then hat * hat.  Otherwise the sinogram is [view][v][u] and dl is
+// computed per pixel.
 template <int NCH, typename ST, bool WEIGHTED>
 __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int jx, int jy, int jz,
                                         const ST *__restrict__ sino_view, float (&acc)[NCH]) {
@@ -96,7 +98,7 @@ __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int 
             if (hb > 0.0f && hz > 0.0f) {
                 float w = hb * hz;
                 if (!WEIGHTED) w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
-                SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc);
+                SinoLoad<NCH, ST>::add(sino_view, WEIGHTED ? (size_t)ju * a.nv + jv : (size_t)jv * a.nu + ju, w, acc);
             }
         }
     }
@@ -155,7 +157,8 @@ __device__ __forceinline__ void bp_view_sep(const ViewGeom &G, const BPArgs &a, 
                         const float rz = fmaf(vp, G.Ev[2], G.Wc[2]) * rinv;
                         w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
                     }
-                    SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc[zz]);
+                    SinoLoad<NCH, ST>::add(sino_view, WEIGHTED ? (size_t)ju * a.nv + jv : (size_t)jv * a.nu + ju, w,
+                                           acc[zz]);
                 }
             }
         }
@@ -248,8 +251,111 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
     }
 }
 
+// Separable geometry, weighted column-major sinogram: the solver's hot path.
+// One warp per (x, y) voxel column, lanes along z.  All lanes of a warp share
+// the voxel column's projected u range and detector-column quantities, which
+// the lanes compute in parallel (lane l: column ulo + l) and broadcast with
+// shuffles; each lane then walks its own exact v window, reading contiguous
+// stretches of the column-major sinogram.  The block's 8 x 32 output tile is
+// transposed through shared memory so the volume stores stay in 32-byte runs.
+constexpr int BZ_COLS = 8;
+
+template <int NCH, typename ST>
+__global__ void __launch_bounds__(32 * BZ_COLS)
+    k_backproject_zl(BPArgs a, const ST *__restrict__ sino, float *__restrict__ out, int accumulate) {
+    __shared__ ViewGeom Gs[BP_CHUNK];
+    __shared__ float otile[NCH][32][BZ_COLS + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int jx = blockIdx.x * BZ_COLS + w, jy = blockIdx.y, jz = blockIdx.z * 32 + lane;
+    const bool colok = jx < a.n;
+    const float ic = 0.5f * (float)(a.n - 1);
+    const float cu = 0.5f * (float)(a.nu - 1), cv = 0.5f * (float)(a.nv - 1);
+    const float cx = (float)jx - ic, cy = (float)jy - ic, cz = (float)jz - ic;
+    float acc[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
+    const size_t view_elems = (size_t)a.nu * a.nv;
+    for (int c0 = 0; c0 < a.nviews; c0 += BP_CHUNK) {
+        const int cn = min(BP_CHUNK, a.nviews - c0);
+        __syncthreads();
+        stage_views<ST>(Gs, a, c0, cn, threadIdx.x, 32 * BZ_COLS);
+        __syncthreads();
+        if (!colok) continue;
+        for (int vi = 0; vi < cn; ++vi) {
+            const ViewGeom &G = Gs[vi];
+            const ST *__restrict__ sv = sino + (size_t)(c0 + vi) * view_elems;
+            // projected u range of the voxel column (warp-uniform)
+            const float X = (float)jx - G.S[0], Y = (float)jy - G.S[1];
+            const float q0 = fmaf(G.Q[1], Y, G.Q[0] * X);
+            const float q2 = fmaf(G.Q[7], Y, G.Q[6] * X);
+            const float u0 = q0 * __frcp_rn(q2);
+            const float hu = (fabsf(G.Q[0] - u0 * G.Q[6]) + fabsf(G.Q[1] - u0 * G.Q[7])) * __frcp_rn(q2 - G.m2);
+            const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
+            const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
+            for (int cb0 = ulo; cb0 <= uhi; cb0 += 32) {
+                const int ncols = min(32, uhi - cb0 + 1);
+                // lane-parallel column set-up
+                float hb = 0.0f, Eb = 0.0f, E1 = 1.0f, rE1 = 1.0f;
+                if (lane < ncols) {
+                    const float up = (float)(cb0 + lane) - cu;
+                    const float wx = __fmaf_rn(up, G.Eu[0], G.Wc[0]);
+                    const float wy = __fmaf_rn(up, G.Eu[1], G.Wc[1]);
+                    const int ax = fabsf(wy) > fabsf(wx) ? 1 : 0;
+                    const float wa = ax ? wy : wx, wb = ax ? wx : wy;
+                    const float rinv = __frcp_rn(wa);
+                    const float *N = ax ? G.NY : G.NX;
+                    const float ca = ax ? cy : cx, cbv = ax ? cx : cy;
+                    hb = 1.0f - fabsf(fmaf(ca, wb * rinv, fmaf(up, N[1], N[0]) * rinv) - cbv);
+                    Eb = fmaf(ca, G.Wc[2], fmaf(up, N[4], N[3])) * rinv;
+                    E1 = fmaf(ca, G.Ev[2], N[5]) * rinv;
+                    rE1 = __frcp_rn(E1);
+                }
+                for (int c = 0; c < ncols; ++c) {
+                    const float hbc = __shfl_sync(0xffffffffu, hb, c);
+                    if (hbc <= 0.0f) continue;
+                    const float Ebc = __shfl_sync(0xffffffffu, Eb, c);
+                    const float E1c = __shfl_sync(0xffffffffu, E1, c);
+                    const float rEc = __shfl_sync(0xffffffffu, rE1, c);
+                    const float E0 = Ebc - cz;
+                    const float centre = fmaf(-E0, rEc, cv), hw = fabsf(rEc);
+                    const int vlo = max(0, (int)ceilf(centre - hw - 1e-3f));
+                    const int vhi = min(a.nv - 1, (int)floorf(centre + hw + 1e-3f));
+                    const ST *__restrict__ colp = sv + (size_t)(cb0 + c) * a.nv;
+                    float ez = fmaf((float)vlo - cv, E1c, E0);
+                    float sacc[NCH];
+#pragma unroll
+                    for (int q = 0; q < NCH; ++q) sacc[q] = 0.0f;
+                    for (int jv = vlo; jv <= vhi; ++jv) {
+                        const float hz = fmaxf(0.0f, 1.0f - fabsf(ez));
+                        SinoLoad<NCH, ST>::add(colp, jv, hz, sacc);
+                        ez += E1c;
+                    }
+#pragma unroll
+                    for (int q = 0; q < NCH; ++q) acc[q] = fmaf(hbc, sacc[q], acc[q]);
+                }
+            }
+        }
+    }
+    // transpose the 8 (x) x 32 (z) tile through shared memory for the stores
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) otile[q][lane][w] = acc[q];
+    __syncthreads();
+    const int zl = threadIdx.x / BZ_COLS, xl = threadIdx.x % BZ_COLS;
+    const int x = blockIdx.x * BZ_COLS + xl, z = blockIdx.z * 32 + zl;
+    if (x < a.n && z < a.n) {
+        const size_t idx = ((size_t)z * a.n + jy) * a.n + x;
+        const size_t nvox = (size_t)a.n * a.n * a.n;
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) {
+            float v = otile[q][zl][xl];
+            if (accumulate) v += out[idx + q * nvox];
+            out[idx + q * nvox] = v;
+        }
+    }
+}
+
 // NCH = 2 writes channel c to out + c * n^3.  WEIGHTED: the sinogram carries
-// each ray's dl already (internal solver path).
+// each ray's dl already and is column-major (internal solver path).
 template <int NCH, typename ST, bool WEIGHTED = false>
 int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int stride, const ST *sino,
                        float *out, int accumulate, cudaStream_t s) {
@@ -263,7 +369,11 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
     a.view0 = view0;
     a.stride = stride;
     a.nviews = nviews;
-    if (g->separable) {
+    if (g->separable && WEIGHTED) {
+        dim3 grid((L.n + BZ_COLS - 1) / BZ_COLS, L.n, (L.n + 31) / 32);
+        MGCT_KERNEL(KK_BACKPROJECT, s,
+                    k_backproject_zl<NCH, ST><<<grid, 32 * BZ_COLS, 0, s>>>(a, sino, out, accumulate));
+    } else if (g->separable) {
         const int zper = BP_BZ * BPS_ZB;
         dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + zper - 1) / zper);
         MGCT_KERNEL(KK_BACKPROJECT, s,

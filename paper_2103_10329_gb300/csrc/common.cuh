@@ -199,6 +199,21 @@ __device__ __forceinline__ DF df_affine(float c, float c_lo, float a, float a_lo
 }
 
 // ---------------------------------------------------------------------------
+// Projector launch shape (shared with the buffers sized for its per-block
+// partial sums): 32 x 8 pixel tiles, views in groups of PJ_VG.
+// ---------------------------------------------------------------------------
+constexpr int PJ_BX = 32;  // detector columns per block
+constexpr int PJ_BY = 8;   // detector rows per block
+constexpr int PJ_VG = 32;  // views per block group
+
+inline size_t project_blocks(int nu, int nv, int nviews) {
+    if (nviews <= 0) return 0;
+    const size_t groups = (size_t)(nviews + PJ_VG - 1) / PJ_VG;
+    const size_t vg = nviews < PJ_VG ? nviews : PJ_VG;
+    return (size_t)((nu + PJ_BX - 1) / PJ_BX) * vg * groups * ((nv + PJ_BY - 1) / PJ_BY);
+}
+
+// ---------------------------------------------------------------------------
 // Internal kernels used across translation units (host launchers)
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -291,7 +291,7 @@ int mgct_geometry_create(const mgct_geom_desc *d, mgct_geom **out) {
     }
     size_t nvox = (size_t)d->n * d->n * d->n;
     // partials: one per projector block (32 x 8 pixels per view), two values each
-    size_t blocks = (size_t)((d->nu + 31) / 32) * ((d->nv + 7) / 8) * K;
+    size_t blocks = project_blocks(d->nu, d->nv, K);
     size_t vblocks = (nvox + 255) / 256;
     g->scratch_part_count = 2 * (blocks > vblocks ? blocks : vblocks) + 64;
     st = check_cuda(cudaMalloc(&g->d_scratch_vol, nvox * 4), "allocate scratch volume");

@@ -73,7 +73,7 @@ int mgct_project_residual_static(const mgct_geom *g, int level, int view0, int n
     if (nvox > NOALLOC_MAX_VOXELS)
         return set_error(MGCT_ESHAPE, "mgct_project_residual_static: volume of " + std::to_string(L.n) +
                                           "^3 voxels exceeds the static scratch (at most 128^3 voxels)");
-    const size_t blocks = (size_t)((L.nu + PJ_BX - 1) / PJ_BX) * ((L.nv + PJ_BY - 1) / PJ_BY) * nviews;
+    const size_t blocks = project_blocks(L.nu, L.nv, nviews);
     if (blocks > NOALLOC_MAX_PARTIALS)
         return set_error(MGCT_ESHAPE, "mgct_project_residual_static: " + std::to_string(blocks) +
                                           " projector blocks exceed the static scratch (at most 262144; "
@@ -88,7 +88,7 @@ int mgct_project_residual_static(const mgct_geom *g, int level, int view0, int n
     // transposed volume in full, one partial per projector block
     MGCT_TRY(launch_transpose_xy<float>(L.n, vol, volT, s));
     int nb = 0;
-    EpiResidual<float> e{out, b, part, L.nu, L.nv};
+    EpiResidual<float> e{out, b, part, L.nu, L.nv, nviews};
     MGCT_TRY(launch_project<float>(g, level, view0, nviews, stride, vol, volT, e, s, &nb));
     return launch_sum_partials(part, nb, 1, sumsq, s);
 }

@@ -15,8 +15,6 @@
 
 namespace mgct {
 
-constexpr int PJ_BX = 32;  // detector columns per block
-constexpr int PJ_BY = 8;   // detector rows per block
 
 struct ProjArgs {
     const ViewGeom *views;
@@ -160,18 +158,27 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
 // with A vol = acc * dlh at that ray, called by every thread of the block
 // (block reductions inside).  "Weighted" sinograms carry the factor dlh of
 // their ray, which the back-projector then need not recompute.
+// Block order.  Consecutive views of the trajectory have nearby source
+// heights, and one detector-row tile of nearby views meets only a z-band of
+// the volume, so blocks are ordered (group of PJ_VG views, row tile, view in
+// group, column tile): the blocks resident at any time share that band and
+// its rows stay in L2.
+
 template <typename VT, typename Epi>
 __global__ void __launch_bounds__(PJ_BX *PJ_BY)
     k_project(ProjArgs a, const VT *__restrict__ vol, const VT *__restrict__ volT, Epi epi) {
     __shared__ ViewGeom G;
-    const int i = blockIdx.z;
-    const int k = a.view0 + i * a.stride;
+    const int vtiles = (a.nv + PJ_BY - 1) / PJ_BY;
+    const int group = blockIdx.z / vtiles, vt = blockIdx.z % vtiles;
+    const int i = group * PJ_VG + blockIdx.y;  // batch index
+    const bool view_ok = i < a.nviews;
+    const int k = a.view0 + (view_ok ? i : 0) * a.stride;
     const int tid = threadIdx.x + threadIdx.y * PJ_BX;
     if (tid < 64) reinterpret_cast<float *>(&G)[tid] = __ldg(reinterpret_cast<const float *>(a.views + k) + tid);
     __syncthreads();
     const int ju = blockIdx.x * PJ_BX + threadIdx.x;
-    const int jv = blockIdx.y * PJ_BY + threadIdx.y;
-    const bool active = ju < a.nu && jv < a.nv;
+    const int jv = vt * PJ_BY + threadIdx.y;
+    const bool active = view_ok && ju < a.nu && jv < a.nv;
     RaySum rs{0.0f, 0.0f};
     if (active) rs = ray_integral(G, a, ju, jv, vol, volT);
     epi(i, k, jv, ju, active, rs.acc, rs.dlh);
@@ -187,28 +194,54 @@ struct EpiStore {
     }
 };
 
-// r = b - A vol; out = r (WEIGHTED: r * dlh), and the block's sum of r^2
-// (float64) into part[block]
+// Weighted sinograms are stored column-major per view, [view][u][v] (v
+// fastest), the layout the back-projector's z-lanes read contiguously.  The
+// epilogues stage the block's 32 x 8 tile in shared memory so that these
+// stores and loads stay in 32-byte runs.
+__device__ __forceinline__ size_t colmajor_index(int i, int ju, int jv, int nu, int nv) {
+    return ((size_t)i * nu + ju) * nv + jv;
+}
+
+// Block tile origin (u0, v0) of the current projector block.
+__device__ __forceinline__ void tile_origin(int nv, int &u0, int &v0) {
+    const int vtiles = (nv + PJ_BY - 1) / PJ_BY;
+    u0 = blockIdx.x * PJ_BX;
+    v0 = (blockIdx.z % vtiles) * PJ_BY;
+}
+
+// r = b - A vol and the block's sum of r^2 (float64) into part[block].
+// WEIGHTED = false: out[i][v][u] = r.  WEIGHTED = true: out[i][u][v] = r * dlh.
 template <typename OT, bool WEIGHTED = false>
 struct EpiResidual {
     OT *out;
-    const float *b;  // indexed like out
+    const float *b;  // [i][v][u], the caller's layout
     double *part;    // NULL: no norm
-    int nu, nv;
+    int nu, nv, nviews;
     __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
         double s[1] = {0.0};
+        float r = 0.0f;
         if (active) {
             size_t idx = ((size_t)i * nv + jv) * nu + ju;
-            float r = __ldg(b + idx) - acc * dlh;
-            if (WEIGHTED) {
-                out[idx] = from_f32<OT>(r * dlh);
-                s[0] = (double)r * (double)r;
-            } else {
+            r = __ldg(b + idx) - acc * dlh;
+            if (!WEIGHTED) {
                 OT ro = from_f32<OT>(r);
                 out[idx] = ro;
                 float rf = to_f32(ro);
                 s[0] = (double)rf * (double)rf;
+            } else {
+                s[0] = (double)r * (double)r;
             }
+        }
+        if (WEIGHTED) {
+            __shared__ float tile[PJ_BX][PJ_BY + 1];
+            tile[threadIdx.x][threadIdx.y] = r * dlh;
+            __syncthreads();
+            const int t = threadIdx.x + threadIdx.y * PJ_BX;
+            const int tu = t / PJ_BY, tv = t % PJ_BY;
+            int u0, v0;
+            tile_origin(nv, u0, v0);
+            if (u0 + tu < nu && v0 + tv < nv && active_view(i))
+                out[colmajor_index(i, u0 + tu, v0 + tv, nu, nv)] = from_f32<OT>(tile[tu][tv]);
         }
         if (part) {
             __shared__ double red[PJ_BX * PJ_BY / 32];
@@ -216,20 +249,32 @@ struct EpiResidual {
             if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = s[0];
         }
     }
+    __device__ bool active_view(int i) const { return i < nviews; }
 };
 
 // Line-search dot products per block, no sinogram write:
-//   <r, A d> = sum r_w * acc  (r_w = r * dlh, the weighted residual)
+//   <r, A d> = sum r_w * acc  (r_w = r * dlh, the weighted residual, [i][u][v])
 //   |A d|^2  = sum (acc * dlh)^2
 template <typename RT>
 struct EpiDualDot {
-    const RT *rw;  // weighted residual, batch sinogram
+    const RT *rw;
     double *part;  // [blocks][2]
-    int nu, nv;
+    int nu, nv, nviews;
     __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
+        __shared__ float tile[PJ_BX][PJ_BY + 1];
+        {
+            const int t = threadIdx.x + threadIdx.y * PJ_BX;
+            const int tu = t / PJ_BY, tv = t % PJ_BY;
+            int u0, v0;
+            tile_origin(nv, u0, v0);
+            float v = 0.0f;
+            if (i < nviews && u0 + tu < nu && v0 + tv < nv) v = to_f32(rw[colmajor_index(i, u0 + tu, v0 + tv, nu, nv)]);
+            tile[tu][tv] = v;
+        }
+        __syncthreads();
         double s[2] = {0.0, 0.0};
         if (active) {
-            float rv = to_f32(rw[((size_t)i * nv + jv) * nu + ju]);
+            float rv = tile[threadIdx.x][threadIdx.y];
             float ad = acc * dlh;
             s[0] = (double)rv * (double)acc;
             s[1] = (double)ad * (double)ad;
@@ -247,21 +292,28 @@ struct EpiDualDot {
 // OS-EMTR (Eq. 3) sinogram terms for one subset, weighted by dlh:
 //   t = exp(-A mu);  c0 = (t - exp(-b)) dlh  (I/I0 = exp(-b));  c1 = t PI dlh
 // b and PI are full [K][nv][nu] arrays indexed by the view k; c is a batch
-// two-channel sinogram.
+// two-channel sinogram [i][u][v][2].
 struct EpiEMTerms {
     float2 *c;
     const float *b;
     const float *pi;
-    int nu, nv;
+    int nu, nv, nviews;
     __device__ void operator()(int i, int k, int jv, int ju, bool active, float acc, float dlh) const {
-        if (!active) return;
-        size_t pix = (size_t)jv * nu + ju;
-        size_t full = (size_t)k * nv * nu + pix;
-        float t = expf(-acc * dlh);
-        float2 o;
-        o.x = (t - expf(-__ldg(b + full))) * dlh;
-        o.y = t * __ldg(pi + full) * dlh;
-        c[(size_t)i * nv * nu + pix] = o;
+        float2 o = make_float2(0.0f, 0.0f);
+        if (active) {
+            size_t full = ((size_t)k * nv + jv) * nu + ju;
+            float t = expf(-acc * dlh);
+            o.x = (t - expf(-__ldg(b + full))) * dlh;
+            o.y = t * __ldg(pi + full) * dlh;
+        }
+        __shared__ float2 tile[PJ_BX][PJ_BY + 1];
+        tile[threadIdx.x][threadIdx.y] = o;
+        __syncthreads();
+        const int t = threadIdx.x + threadIdx.y * PJ_BX;
+        const int tu = t / PJ_BY, tv = t % PJ_BY;
+        int u0, v0;
+        tile_origin(nv, u0, v0);
+        if (i < nviews && u0 + tu < nu && v0 + tv < nv) c[colmajor_index(i, u0 + tu, v0 + tv, nu, nv)] = tile[tu][tv];
     }
 };
 
@@ -278,8 +330,10 @@ int launch_project(const mgct_geom *g, int level, int view0, int nviews, int str
     a.view0 = view0;
     a.stride = stride;
     a.nviews = nviews;
-    dim3 grid((L.nu + PJ_BX - 1) / PJ_BX, (L.nv + PJ_BY - 1) / PJ_BY, nviews);
-    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+    const int groups = (nviews + PJ_VG - 1) / PJ_VG;
+    const int vg = nviews < PJ_VG ? nviews : PJ_VG;
+    dim3 grid((L.nu + PJ_BX - 1) / PJ_BX, vg, groups * ((L.nv + PJ_BY - 1) / PJ_BY));
+    if (nblocks) *nblocks = (int)project_blocks(L.nu, L.nv, nviews);
     if (nviews == 0) return MGCT_OK;
     MGCT_KERNEL(KK_PROJECT, s, k_project<VT, Epi><<<grid, dim3(PJ_BX, PJ_BY), 0, s>>>(a, vol, volT, epi));
     return MGCT_OK;

@@ -43,7 +43,7 @@ static size_t sino_elems(const mgct_geom *g, const LevelInfo &L) {
     return (size_t)g->desc.n_views * L.nv * L.nu;
 }
 static size_t proj_blocks(const mgct_geom *g, const LevelInfo &L) {
-    return (size_t)((L.nu + PJ_BX - 1) / PJ_BX) * ((L.nv + PJ_BY - 1) / PJ_BY) * g->desc.n_views;
+    return project_blocks(L.nu, L.nv, g->desc.n_views);
 }
 
 struct LWSpace {
@@ -144,7 +144,7 @@ static int landweber(const mgct_geom *g, int level, float *mu, const float *b, v
     MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
     int nb = 0;
     // r is stored weighted by each ray's dl, which the back-projector then skips
-    EpiResidual<float, true> er{w.r, b, w.part, L.nu, L.nv};
+    EpiResidual<float, true> er{w.r, b, w.part, L.nu, L.nv, K};
     MGCT_TRY(launch_project<float>(g, level, 0, K, 1, mu, w.muT, er, s, &nb));
     MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
     // d = p * A^T r   (or A^T r for SIRT)
@@ -158,7 +158,7 @@ static int landweber(const mgct_geom *g, int level, float *mu, const float *b, v
     if (!(o.alpha > 0.0)) {
         // exact line search along d: <r, A d>, |A d|^2
         MGCT_TRY(launch_transpose_xy<float>(L.n, d, dT, s));
-        EpiDualDot<float> ed{w.r, w.part, L.nu, L.nv};
+        EpiDualDot<float> ed{w.r, w.part, L.nu, L.nv, K};
         MGCT_TRY(launch_project<float>(g, level, 0, K, 1, d, dT, ed, s, &nb));
         MGCT_TRY(launch_sum_partials(w.part, nb, 2, w.sums + 1, s));
     }
@@ -179,7 +179,7 @@ static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *
         int cnt = (K - m + M - 1) / M;
         if (cnt <= 0) continue;
         MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
-        EpiEMTerms e{w.c2, b, pi, L.nu, L.nv};
+        EpiEMTerms e{w.c2, b, pi, L.nu, L.nv, cnt};
         MGCT_TRY(launch_project<float>(g, level, m, cnt, M, mu, w.muT, e, s));
         MGCT_TRY(launch_backproject<2, float2, true>(g, level, m, cnt, M, w.c2, w.nd, 0, s));
         MGCT_TRY(launch_em_update(nv3, mu, w.nd, w.part, s));
@@ -247,7 +247,7 @@ int mgct_project(const mgct_geom *g, int level, int view0, int nviews, int strid
         VT *vT = static_cast<VT *>(g->d_scratch_vol);
         MGCT_TRY(launch_transpose_xy<VT>(L.n, v, vT, s));
         if (b) {
-            EpiResidual<OT> e{static_cast<OT *>(out), b, part, L.nu, L.nv};
+            EpiResidual<OT> e{static_cast<OT *>(out), b, part, L.nu, L.nv, nviews};
             return launch_project<VT>(g, level, view0, nviews, stride, v, vT, e, s, &nb);
         }
         EpiStore<OT> e{static_cast<OT *>(out), L.nu, L.nv};

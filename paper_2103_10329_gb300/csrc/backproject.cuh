@@ -253,21 +253,22 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
 
 // Separable geometry, weighted column-major sinogram: the solver's hot path.
 // One warp per (x, y) voxel column, lanes along z.  All lanes of a warp share
-// the voxel column's projected u range and detector-column quantities, which
-// the lanes compute in parallel (lane l: column ulo + l) and broadcast with
-// shuffles; each lane then walks its own exact v window, reading contiguous
-// stretches of the column-major sinogram.  The block's 8 x 32 output tile is
-// transposed through shared memory so the volume stores stay in 32-byte runs.
+// the voxel column's projected u range (computed lane-parallel for 32 views
+// at a time) and the detector-column quantities (lane l sets up column
+// ulo + l from the column table; shuffles broadcast them); each lane then
+// walks its own exact v window, reading contiguous stretches of the
+// column-major sinogram.  The block's 8 x 32 output tile is transposed
+// through shared memory so the volume stores stay in 32-byte runs.
 constexpr int BZ_COLS = 8;
 
 template <int NCH, typename ST>
-__global__ void __launch_bounds__(32 * BZ_COLS)
-    k_backproject_zl(BPArgs a, const ST *__restrict__ sino, float *__restrict__ out, int accumulate) {
-    __shared__ ViewGeom Gs[BP_CHUNK];
+__global__ void __launch_bounds__(32 * BZ_COLS, 4)
+    k_backproject_zl(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
+                     float *__restrict__ out, int accumulate) {
     __shared__ float otile[NCH][32][BZ_COLS + 1];
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int jx = blockIdx.x * BZ_COLS + w, jy = blockIdx.y, jz = blockIdx.z * 32 + lane;
-    const bool colok = jx < a.n;
     const float ic = 0.5f * (float)(a.n - 1);
     const float cu = 0.5f * (float)(a.nu - 1), cv = 0.5f * (float)(a.nv - 1);
     const float cx = (float)jx - ic, cy = (float)jy - ic, cz = (float)jz - ic;
@@ -275,63 +276,63 @@ __global__ void __launch_bounds__(32 * BZ_COLS)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
     const size_t view_elems = (size_t)a.nu * a.nv;
-    for (int c0 = 0; c0 < a.nviews; c0 += BP_CHUNK) {
-        const int cn = min(BP_CHUNK, a.nviews - c0);
-        __syncthreads();
-        stage_views<ST>(Gs, a, c0, cn, threadIdx.x, 32 * BZ_COLS);
-        __syncthreads();
-        if (!colok) continue;
-        for (int vi = 0; vi < cn; ++vi) {
-            const ViewGeom &G = Gs[vi];
-            const ST *__restrict__ sv = sino + (size_t)(c0 + vi) * view_elems;
-            // projected u range of the voxel column (warp-uniform)
-            const float X = (float)jx - G.S[0], Y = (float)jy - G.S[1];
-            const float q0 = fmaf(G.Q[1], Y, G.Q[0] * X);
-            const float q2 = fmaf(G.Q[7], Y, G.Q[6] * X);
-            const float u0 = q0 * __frcp_rn(q2);
-            const float hu = (fabsf(G.Q[0] - u0 * G.Q[6]) + fabsf(G.Q[1] - u0 * G.Q[7])) * __frcp_rn(q2 - G.m2);
-            const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
-            const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
-            for (int cb0 = ulo; cb0 <= uhi; cb0 += 32) {
-                const int ncols = min(32, uhi - cb0 + 1);
-                // lane-parallel column set-up
-                float hb = 0.0f, Eb = 0.0f, E1 = 1.0f, rE1 = 1.0f;
-                if (lane < ncols) {
-                    const float up = (float)(cb0 + lane) - cu;
-                    const float wx = __fmaf_rn(up, G.Eu[0], G.Wc[0]);
-                    const float wy = __fmaf_rn(up, G.Eu[1], G.Wc[1]);
-                    const int ax = fabsf(wy) > fabsf(wx) ? 1 : 0;
-                    const float wa = ax ? wy : wx, wb = ax ? wx : wy;
-                    const float rinv = __frcp_rn(wa);
-                    const float *N = ax ? G.NY : G.NX;
-                    const float ca = ax ? cy : cx, cbv = ax ? cx : cy;
-                    hb = 1.0f - fabsf(fmaf(ca, wb * rinv, fmaf(up, N[1], N[0]) * rinv) - cbv);
-                    Eb = fmaf(ca, G.Wc[2], fmaf(up, N[4], N[3])) * rinv;
-                    E1 = fmaf(ca, G.Ev[2], N[5]) * rinv;
-                    rE1 = __frcp_rn(E1);
-                }
-                for (int c = 0; c < ncols; ++c) {
-                    const float hbc = __shfl_sync(0xffffffffu, hb, c);
-                    if (hbc <= 0.0f) continue;
-                    const float Ebc = __shfl_sync(0xffffffffu, Eb, c);
-                    const float E1c = __shfl_sync(0xffffffffu, E1, c);
-                    const float rEc = __shfl_sync(0xffffffffu, rE1, c);
-                    const float E0 = Ebc - cz;
-                    const float centre = fmaf(-E0, rEc, cv), hw = fabsf(rEc);
-                    const int vlo = max(0, (int)ceilf(centre - hw - 1e-3f));
-                    const int vhi = min(a.nv - 1, (int)floorf(centre + hw + 1e-3f));
-                    const ST *__restrict__ colp = sv + (size_t)(cb0 + c) * a.nv;
-                    float ez = fmaf((float)vlo - cv, E1c, E0);
-                    float sacc[NCH];
-#pragma unroll
-                    for (int q = 0; q < NCH; ++q) sacc[q] = 0.0f;
-                    for (int jv = vlo; jv <= vhi; ++jv) {
-                        const float hz = fmaxf(0.0f, 1.0f - fabsf(ez));
-                        SinoLoad<NCH, ST>::add(colp, jv, hz, sacc);
-                        ez += E1c;
+    if (jx < a.n) {
+        for (int c0 = 0; c0 < a.nviews; c0 += 32) {
+            const int cn = min(32, a.nviews - c0);
+            // lane l: projected u range of this voxel column in view c0 + l
+            int my_lo = 0, my_hi = -1;
+            if (lane < cn) {
+                const float *G = reinterpret_cast<const float *>(a.views + a.view0 + (c0 + lane) * a.stride);
+                const float X = (float)jx - __ldg(G + 0), Y = (float)jy - __ldg(G + 1);
+                const float Q0 = __ldg(G + 12), Q1 = __ldg(G + 13), Q6 = __ldg(G + 18), Q7 = __ldg(G + 19);
+                const float q2 = fmaf(Q7, Y, Q6 * X);
+                const float u0 = fmaf(Q1, Y, Q0 * X) * __frcp_rn(q2);
+                const float hu = (fabsf(Q0 - u0 * Q6) + fabsf(Q1 - u0 * Q7)) * __frcp_rn(q2 - __ldg(G + 21));
+                my_lo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
+                my_hi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
+            }
+            for (int vi = 0; vi < cn; ++vi) {
+                const int ulo = __shfl_sync(full, my_lo, vi);
+                const int uhi = __shfl_sync(full, my_hi, vi);
+                const int k = a.view0 + (c0 + vi) * a.stride;
+                const ST *__restrict__ sv = sino + (size_t)(c0 + vi) * view_elems;
+                const float4 *__restrict__ ct = cols + (size_t)k * a.nu * 2;
+                for (int cb0 = ulo; cb0 <= uhi; cb0 += 32) {
+                    const int ncols = min(32, uhi - cb0 + 1);
+                    float hb = 0.0f, Eb = 0.0f, E1 = 1.0f, rE1 = 1.0f;
+                    if (lane < ncols) {
+                        const float4 t0 = __ldg(ct + 2 * (cb0 + lane));
+                        const float4 t1 = __ldg(ct + 2 * (cb0 + lane) + 1);
+                        const bool ay = t0.x != 0.0f;
+                        const float ca = ay ? cy : cx, cbv = ay ? cx : cy;
+                        hb = 1.0f - fabsf(fmaf(ca, t0.y, t0.z) - cbv);
+                        Eb = fmaf(ca, t1.x, t0.w);
+                        E1 = fmaf(ca, t1.z, t1.y);
+                        rE1 = __frcp_rn(E1);
                     }
+                    for (int c = 0; c < ncols; ++c) {
+                        const float hbc = __shfl_sync(full, hb, c);
+                        if (hbc <= 0.0f) continue;
+                        const float Ebc = __shfl_sync(full, Eb, c);
+                        const float E1c = __shfl_sync(full, E1, c);
+                        const float rEc = __shfl_sync(full, rE1, c);
+                        const float E0 = Ebc - cz;
+                        const float centre = fmaf(-E0, rEc, cv), hw = fabsf(rEc);
+                        const int vlo = max(0, (int)ceilf(centre - hw - 1e-3f));
+                        const int vhi = min(a.nv - 1, (int)floorf(centre + hw + 1e-3f));
+                        const ST *__restrict__ colp = sv + (size_t)(cb0 + c) * a.nv;
+                        float ez = fmaf((float)vlo - cv, E1c, E0);
+                        float sacc[NCH];
 #pragma unroll
-                    for (int q = 0; q < NCH; ++q) acc[q] = fmaf(hbc, sacc[q], acc[q]);
+                        for (int q = 0; q < NCH; ++q) sacc[q] = 0.0f;
+#pragma unroll 2
+                        for (int jv = vlo; jv <= vhi; ++jv) {
+                            SinoLoad<NCH, ST>::add(colp, jv, fmaxf(0.0f, 1.0f - fabsf(ez)), sacc);
+                            ez += E1c;
+                        }
+#pragma unroll
+                        for (int q = 0; q < NCH; ++q) acc[q] = fmaf(hbc, sacc[q], acc[q]);
+                    }
                 }
             }
         }
@@ -354,6 +355,23 @@ __global__ void __launch_bounds__(32 * BZ_COLS)
     }
 }
 
+// Column table (see LevelInfo::d_cols): one thread per (view, column); the
+// axis choice is the projector's own ray_dir() at v' = 0.
+__global__ void k_column_table(const ViewGeom *__restrict__ views, int K, int nu, float4 *__restrict__ cols) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K * nu) return;
+    const int k = t / nu, ju = t % nu;
+    const ViewGeom &G = views[k];
+    const float up = (float)ju - 0.5f * (float)(nu - 1);
+    const RayDir d = ray_dir(G, up, 0.0f);
+    const float wa = d.ax ? d.wy : d.wx, wb = d.ax ? d.wx : d.wy;
+    const float rinv = __frcp_rn(wa);
+    const float *N = d.ax ? G.NY : G.NX;
+    cols[2 * (size_t)t] = make_float4(d.ax ? 1.0f : 0.0f, wb * rinv, fmaf(up, N[1], N[0]) * rinv,
+                                      fmaf(up, N[4], N[3]) * rinv);
+    cols[2 * (size_t)t + 1] = make_float4(G.Wc[2] * rinv, N[5] * rinv, G.Ev[2] * rinv, 0.0f);
+}
+
 // NCH = 2 writes channel c to out + c * n^3.  WEIGHTED: the sinogram carries
 // each ray's dl already and is column-major (internal solver path).
 template <int NCH, typename ST, bool WEIGHTED = false>
@@ -369,10 +387,10 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
     a.view0 = view0;
     a.stride = stride;
     a.nviews = nviews;
-    if (g->separable && WEIGHTED) {
+    if (g->separable && WEIGHTED && L.d_cols) {
         dim3 grid((L.n + BZ_COLS - 1) / BZ_COLS, L.n, (L.n + 31) / 32);
         MGCT_KERNEL(KK_BACKPROJECT, s,
-                    k_backproject_zl<NCH, ST><<<grid, 32 * BZ_COLS, 0, s>>>(a, sino, out, accumulate));
+                    k_backproject_zl<NCH, ST><<<grid, 32 * BZ_COLS, 0, s>>>(a, L.d_cols, sino, out, accumulate));
     } else if (g->separable) {
         const int zper = BP_BZ * BPS_ZB;
         dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + zper - 1) / zper);

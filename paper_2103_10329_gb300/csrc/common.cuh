@@ -58,7 +58,17 @@ struct LevelInfo {
     int n, nu, nv;
     double h, pitch;
     ViewGeom *d_views;  // device [K]
+    float4 *d_cols;     // device [K][nu][2] detector-column table (separable geometries), or NULL
 };
+
+// Detector-column table of a separable geometry (no detector tilt): for view
+// k and column u' every ray of the column has the same major axis and
+// horizontal slope, and its z crossing is linear in v'.  With (c_a, c_b) the
+// centred voxel coordinates along the column's major axis and the other
+// horizontal axis, the back-projector needs
+//   e_b = c_a rb + pb - c_b,   E0 + c_z = ez0 + c_a ezc,   E1 = e10 + c_a e1c.
+// Entry: {ax, rb, pb, ez0}, {ezc, e10, e1c, 0}.
+int launch_column_table(const mgct_geom *g, int level, cudaStream_t s);
 
 }  // namespace mgct
 

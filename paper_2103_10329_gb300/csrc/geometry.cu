@@ -198,7 +198,14 @@ static int upload_tables(mgct_geom *g) {
                                        cudaMemcpyHostToDevice),
                             "upload view tables"));
     }
-    return MGCT_OK;
+    for (int l = 0; l < g->levels; ++l) {
+        LevelInfo &L = g->lev[l];
+        if (!g->separable) continue;
+        if (!L.d_cols)
+            MGCT_TRY(check_cuda(cudaMalloc(&L.d_cols, (size_t)K * L.nu * 2 * sizeof(float4)), "allocate column table"));
+        MGCT_TRY(launch_column_table(g, l, 0));
+    }
+    return check_cuda(cudaDeviceSynchronize(), "column tables");
 }
 
 }  // namespace mgct
@@ -233,8 +240,10 @@ uint64_t mgct_launch_count(int reset) {
 
 void mgct_geometry_destroy(mgct_geom *g) {
     if (!g) return;
-    for (int l = 0; l < 8; ++l)
+    for (int l = 0; l < 8; ++l) {
         if (g->lev[l].d_views) cudaFree(g->lev[l].d_views);
+        if (g->lev[l].d_cols) cudaFree(g->lev[l].d_cols);
+    }
     if (g->d_scratch_vol) cudaFree(g->d_scratch_vol);
     if (g->d_scratch_part) cudaFree(g->d_scratch_part);
     delete g;

@@ -22,6 +22,14 @@ int launch_em_update(size_t count, float *mu, const float *nd, double *part, cud
 int launch_fill(size_t count, float *x, float v, cudaStream_t s);
 int launch_copy(size_t count, const float *in, float *out, cudaStream_t s);
 
+int launch_column_table(const mgct_geom *g, int level, cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    const int K = g->desc.n_views;
+    const int total = K * L.nu;
+    MGCT_KERNEL(KK_OTHER, s, k_column_table<<<(total + 255) / 256, 256, 0, s>>>(L.d_views, K, L.nu, L.d_cols));
+    return MGCT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Workspace carving
 // ---------------------------------------------------------------------------

@@ -51,11 +51,14 @@ struct SinoLoad<2, float2> {
     }
 };
 
+__device__ __forceinline__ float2 load_f2(const float2 *p) { return __ldg(p); }
+template <typename ST>
+__device__ __forceinline__ float2 load_f2(const ST *) { return make_float2(0.0f, 0.0f); }
+
 // Adds A^T (one view) at voxel (jx, jy, jz) into acc -- any geometry.
 // WEIGHTED: the sinogram already carries each ray's dl (see the projector's
-// weighted epilogues) and is stored column-major per view, [view][u][v]; the
-// weight is then hat * hat.  Otherwise the sinogram is [view][v][u] and dl is
-// computed per pixel.
+// weighted epilogues), so the weight is hat * hat; otherwise dl is computed
+// per pixel.  Sinograms are [view][v][u].
 template <int NCH, typename ST, bool WEIGHTED>
 __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int jx, int jy, int jz,
                                         const ST *__restrict__ sino_view, float (&acc)[NCH]) {
@@ -98,7 +101,7 @@ __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int 
             if (hb > 0.0f && hz > 0.0f) {
                 float w = hb * hz;
                 if (!WEIGHTED) w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
-                SinoLoad<NCH, ST>::add(sino_view, WEIGHTED ? (size_t)ju * a.nv + jv : (size_t)jv * a.nu + ju, w, acc);
+                SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc);
             }
         }
     }
@@ -157,8 +160,7 @@ __device__ __forceinline__ void bp_view_sep(const ViewGeom &G, const BPArgs &a, 
                         const float rz = fmaf(vp, G.Ev[2], G.Wc[2]) * rinv;
                         w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
                     }
-                    SinoLoad<NCH, ST>::add(sino_view, WEIGHTED ? (size_t)ju * a.nv + jv : (size_t)jv * a.nu + ju, w,
-                                           acc[zz]);
+                    SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc[zz]);
                 }
             }
         }
@@ -251,106 +253,104 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
     }
 }
 
-// Separable geometry, weighted column-major sinogram: the solver's hot path.
-// One warp per (x, y) voxel column, lanes along z.  All lanes of a warp share
-// the voxel column's projected u range (computed lane-parallel for 32 views
-// at a time) and the detector-column quantities (lane l sets up column
-// ulo + l from the column table; shuffles broadcast them); each lane then
-// walks its own exact v window, reading contiguous stretches of the
-// column-major sinogram.  The block's 8 x 32 output tile is transposed
-// through shared memory so the volume stores stay in 32-byte runs.
-constexpr int BZ_COLS = 8;
+// Separable geometry, weighted sinogram: the solver's hot path.
+// Each thread owns one (x, y) voxel column and a slab of BS_Z voxels along z,
+// accumulated in shared memory.  Per view and per detector column u' whose
+// rays meet the voxel column (|e_b| < 1), the z crossing of the ray through
+// pixel (u', v') is f_z(v') = E0' + v' E1 (E0' uncentred), so the voxels the
+// ray touches are floor(f_z) and floor(f_z) + 1 with weights (1 - t, t),
+// t = f_z - floor(f_z): the exact transpose of the projector's bilinear tap
+// in z.  Each pixel of the slab's v range is visited once and splatted into
+// the thread's own shared-memory column (no two threads share a column, so
+// no atomics, and the order of additions is fixed).  Lanes are adjacent x
+// columns, so the pixel reads of a warp fall on one detector row.
+constexpr int BS_TX = 32, BS_TY = 4, BS_THREADS = BS_TX * BS_TY;
+
+template <int NCH>
+struct SlabCfg {
+    static constexpr int Z = 64 / NCH;  // voxels per slab
+    static constexpr int ROWS = Z + 4;  // two guard rows at each end
+};
 
 template <int NCH, typename ST>
-__global__ void __launch_bounds__(32 * BZ_COLS, 4)
-    k_backproject_zl(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
-                     float *__restrict__ out, int accumulate) {
-    __shared__ float otile[NCH][32][BZ_COLS + 1];
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int jx = blockIdx.x * BZ_COLS + w, jy = blockIdx.y, jz = blockIdx.z * 32 + lane;
-    const float ic = 0.5f * (float)(a.n - 1);
-    const float cu = 0.5f * (float)(a.nu - 1), cv = 0.5f * (float)(a.nv - 1);
-    const float cx = (float)jx - ic, cy = (float)jy - ic, cz = (float)jz - ic;
-    float acc[NCH];
+__global__ void __launch_bounds__(BS_THREADS)
+    k_backproject_slab(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
+                       float *__restrict__ out, int accumulate) {
+    constexpr int Z = SlabCfg<NCH>::Z, ROWS = SlabCfg<NCH>::ROWS;
+    __shared__ float acc[NCH][ROWS][BS_THREADS];
+    const int tid = threadIdx.x;
+    const int jx = blockIdx.x * BS_TX + (tid % BS_TX), jy = blockIdx.y * BS_TY + tid / BS_TX;
+    const int z0 = blockIdx.z * Z;
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) acc[c] = 0.0f;
-    const size_t view_elems = (size_t)a.nu * a.nv;
-    if (jx < a.n) {
-        for (int c0 = 0; c0 < a.nviews; c0 += 32) {
-            const int cn = min(32, a.nviews - c0);
-            // lane l: projected u range of this voxel column in view c0 + l
-            int my_lo = 0, my_hi = -1;
-            if (lane < cn) {
-                const float *G = reinterpret_cast<const float *>(a.views + a.view0 + (c0 + lane) * a.stride);
-                const float X = (float)jx - __ldg(G + 0), Y = (float)jy - __ldg(G + 1);
-                const float Q0 = __ldg(G + 12), Q1 = __ldg(G + 13), Q6 = __ldg(G + 18), Q7 = __ldg(G + 19);
-                const float q2 = fmaf(Q7, Y, Q6 * X);
-                const float u0 = fmaf(Q1, Y, Q0 * X) * __frcp_rn(q2);
-                const float hu = (fabsf(Q0 - u0 * Q6) + fabsf(Q1 - u0 * Q7)) * __frcp_rn(q2 - __ldg(G + 21));
-                my_lo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
-                my_hi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
-            }
-            for (int vi = 0; vi < cn; ++vi) {
-                const int ulo = __shfl_sync(full, my_lo, vi);
-                const int uhi = __shfl_sync(full, my_hi, vi);
-                const int k = a.view0 + (c0 + vi) * a.stride;
-                const ST *__restrict__ sv = sino + (size_t)(c0 + vi) * view_elems;
-                const float4 *__restrict__ ct = cols + (size_t)k * a.nu * 2;
-                for (int cb0 = ulo; cb0 <= uhi; cb0 += 32) {
-                    const int ncols = min(32, uhi - cb0 + 1);
-                    float hb = 0.0f, Eb = 0.0f, E1 = 1.0f, rE1 = 1.0f;
-                    if (lane < ncols) {
-                        const float4 t0 = __ldg(ct + 2 * (cb0 + lane));
-                        const float4 t1 = __ldg(ct + 2 * (cb0 + lane) + 1);
-                        const bool ay = t0.x != 0.0f;
-                        const float ca = ay ? cy : cx, cbv = ay ? cx : cy;
-                        hb = 1.0f - fabsf(fmaf(ca, t0.y, t0.z) - cbv);
-                        Eb = fmaf(ca, t1.x, t0.w);
-                        E1 = fmaf(ca, t1.z, t1.y);
-                        rE1 = __frcp_rn(E1);
-                    }
-                    for (int c = 0; c < ncols; ++c) {
-                        const float hbc = __shfl_sync(full, hb, c);
-                        if (hbc <= 0.0f) continue;
-                        const float Ebc = __shfl_sync(full, Eb, c);
-                        const float E1c = __shfl_sync(full, E1, c);
-                        const float rEc = __shfl_sync(full, rE1, c);
-                        const float E0 = Ebc - cz;
-                        const float centre = fmaf(-E0, rEc, cv), hw = fabsf(rEc);
-                        const int vlo = max(0, (int)ceilf(centre - hw - 1e-3f));
-                        const int vhi = min(a.nv - 1, (int)floorf(centre + hw + 1e-3f));
-                        const ST *__restrict__ colp = sv + (size_t)(cb0 + c) * a.nv;
-                        float ez = fmaf((float)vlo - cv, E1c, E0);
-                        float sacc[NCH];
-#pragma unroll
-                        for (int q = 0; q < NCH; ++q) sacc[q] = 0.0f;
-#pragma unroll 2
-                        for (int jv = vlo; jv <= vhi; ++jv) {
-                            SinoLoad<NCH, ST>::add(colp, jv, fmaxf(0.0f, 1.0f - fabsf(ez)), sacc);
-                            ez += E1c;
-                        }
-#pragma unroll
-                        for (int q = 0; q < NCH; ++q) acc[q] = fmaf(hbc, sacc[q], acc[q]);
+    for (int q = 0; q < NCH; ++q)
+        for (int r = 0; r < ROWS; ++r) acc[q][r][tid] = 0.0f;
+    if (jx < a.n && jy < a.n) {
+        const float ic = 0.5f * (float)(a.n - 1);
+        const float cu = 0.5f * (float)(a.nu - 1), cv = 0.5f * (float)(a.nv - 1);
+        const float cx = (float)jx - ic, cy = (float)jy - ic;
+        const float zlo = (float)z0 - 1.0f, zhi = (float)(z0 + Z);  // crossings that touch the slab
+        const size_t view_elems = (size_t)a.nu * a.nv;
+        for (int i = 0; i < a.nviews; ++i) {
+            const int k = a.view0 + i * a.stride;
+            const float *G = reinterpret_cast<const float *>(a.views + k);
+            // projected u range of the voxel column (the cube bound; z-free without tilt)
+            const float X = (float)jx - __ldg(G + 0), Y = (float)jy - __ldg(G + 1);
+            const float Q0 = __ldg(G + 12), Q1 = __ldg(G + 13), Q6 = __ldg(G + 18), Q7 = __ldg(G + 19);
+            const float q2 = fmaf(Q7, Y, Q6 * X);
+            const float u0 = fmaf(Q1, Y, Q0 * X) * __frcp_rn(q2);
+            const float hu = (fabsf(Q0 - u0 * Q6) + fabsf(Q1 - u0 * Q7)) * __frcp_rn(q2 - __ldg(G + 21));
+            const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
+            const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
+            const ST *__restrict__ sv = sino + (size_t)i * view_elems;
+            const float4 *__restrict__ ct = cols + (size_t)k * a.nu * 2;
+            for (int ju = ulo; ju <= uhi; ++ju) {
+                const float4 t0 = __ldg(ct + 2 * ju);
+                const float4 t1 = __ldg(ct + 2 * ju + 1);
+                const bool ay = t0.x != 0.0f;
+                const float ca = ay ? cy : cx, cb = ay ? cx : cy;
+                const float hb = 1.0f - fabsf(fmaf(ca, t0.y, t0.z) - cb);
+                if (hb <= 0.0f) continue;
+                const float E0 = fmaf(ca, t1.x, t0.w) + ic;  // uncentred z crossing at v' = 0
+                const float E1 = fmaf(ca, t1.z, t1.y);
+                const float rE = __frcp_rn(E1);
+                const float ta = fmaf(zlo - E0, rE, cv), tb = fmaf(zhi - E0, rE, cv);
+                const int vlo = max(0, (int)ceilf(fminf(ta, tb) - 1e-3f));
+                const int vhi = min(a.nv - 1, (int)floorf(fmaxf(ta, tb) + 1e-3f));
+                float vf = (float)vlo - cv;
+                const ST *__restrict__ px = sv + (size_t)vlo * a.nu + ju;
+                for (int jv = vlo; jv <= vhi; ++jv, vf += 1.0f, px += a.nu) {
+                    const float fz = fmaf(vf, E1, E0);
+                    const float fl = floorf(fz);
+                    const float t = fz - fl;
+                    // row of voxel floor(fz) in the guarded slab: in [0, Z + 2]
+                    const int r = min(max((int)fl - z0 + 2, 0), ROWS - 2);
+                    if constexpr (NCH == 1) {
+                        const float yw = hb * to_f32(__ldg(px));
+                        const float w1 = yw * t;
+                        acc[0][r][tid] += yw - w1;
+                        acc[0][r + 1][tid] += w1;
+                    } else {
+                        const float2 y2 = load_f2(px);
+                        const float ya = hb * y2.x, yb = hb * y2.y;
+                        acc[0][r][tid] += ya - ya * t;
+                        acc[0][r + 1][tid] += ya * t;
+                        acc[NCH - 1][r][tid] += yb - yb * t;
+                        acc[NCH - 1][r + 1][tid] += yb * t;
                     }
                 }
             }
         }
-    }
-    // transpose the 8 (x) x 32 (z) tile through shared memory for the stores
-#pragma unroll
-    for (int q = 0; q < NCH; ++q) otile[q][lane][w] = acc[q];
-    __syncthreads();
-    const int zl = threadIdx.x / BZ_COLS, xl = threadIdx.x % BZ_COLS;
-    const int x = blockIdx.x * BZ_COLS + xl, z = blockIdx.z * 32 + zl;
-    if (x < a.n && z < a.n) {
-        const size_t idx = ((size_t)z * a.n + jy) * a.n + x;
         const size_t nvox = (size_t)a.n * a.n * a.n;
+        for (int zz = 0; zz < Z; ++zz) {
+            const int z = z0 + zz;
+            if (z >= a.n) break;
+            const size_t idx = ((size_t)z * a.n + jy) * a.n + jx;
 #pragma unroll
-        for (int q = 0; q < NCH; ++q) {
-            float v = otile[q][zl][xl];
-            if (accumulate) v += out[idx + q * nvox];
-            out[idx + q * nvox] = v;
+            for (int q = 0; q < NCH; ++q) {
+                float v = acc[q][zz + 2][tid];
+                if (accumulate) v += out[idx + q * nvox];
+                out[idx + q * nvox] = v;
+            }
         }
     }
 }
@@ -373,7 +373,7 @@ __global__ void k_column_table(const ViewGeom *__restrict__ views, int K, int nu
 }
 
 // NCH = 2 writes channel c to out + c * n^3.  WEIGHTED: the sinogram carries
-// each ray's dl already and is column-major (internal solver path).
+// each ray's dl already (internal solver path).
 template <int NCH, typename ST, bool WEIGHTED = false>
 int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int stride, const ST *sino,
                        float *out, int accumulate, cudaStream_t s) {
@@ -388,9 +388,10 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
     a.stride = stride;
     a.nviews = nviews;
     if (g->separable && WEIGHTED && L.d_cols) {
-        dim3 grid((L.n + BZ_COLS - 1) / BZ_COLS, L.n, (L.n + 31) / 32);
+        constexpr int Z = SlabCfg<NCH>::Z;
+        dim3 grid((L.n + BS_TX - 1) / BS_TX, (L.n + BS_TY - 1) / BS_TY, (L.n + Z - 1) / Z);
         MGCT_KERNEL(KK_BACKPROJECT, s,
-                    k_backproject_zl<NCH, ST><<<grid, 32 * BZ_COLS, 0, s>>>(a, L.d_cols, sino, out, accumulate));
+                    k_backproject_slab<NCH, ST><<<grid, BS_THREADS, 0, s>>>(a, L.d_cols, sino, out, accumulate));
     } else if (g->separable) {
         const int zper = BP_BZ * BPS_ZB;
         dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + zper - 1) / zper);

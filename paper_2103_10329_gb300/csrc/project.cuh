@@ -194,54 +194,29 @@ struct EpiStore {
     }
 };
 
-// Weighted sinograms are stored column-major per view, [view][u][v] (v
-// fastest), the layout the back-projector's z-lanes read contiguously.  The
-// epilogues stage the block's 32 x 8 tile in shared memory so that these
-// stores and loads stay in 32-byte runs.
-__device__ __forceinline__ size_t colmajor_index(int i, int ju, int jv, int nu, int nv) {
-    return ((size_t)i * nu + ju) * nv + jv;
-}
-
-// Block tile origin (u0, v0) of the current projector block.
-__device__ __forceinline__ void tile_origin(int nv, int &u0, int &v0) {
-    const int vtiles = (nv + PJ_BY - 1) / PJ_BY;
-    u0 = blockIdx.x * PJ_BX;
-    v0 = (blockIdx.z % vtiles) * PJ_BY;
-}
-
 // r = b - A vol and the block's sum of r^2 (float64) into part[block].
-// WEIGHTED = false: out[i][v][u] = r.  WEIGHTED = true: out[i][u][v] = r * dlh.
+// WEIGHTED = false: out = r.  WEIGHTED = true: out = r * dlh (the ray's path
+// length per plane), which the back-projector then need not recompute.
 template <typename OT, bool WEIGHTED = false>
 struct EpiResidual {
     OT *out;
-    const float *b;  // [i][v][u], the caller's layout
+    const float *b;  // indexed like out
     double *part;    // NULL: no norm
     int nu, nv, nviews;
     __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
         double s[1] = {0.0};
-        float r = 0.0f;
         if (active) {
             size_t idx = ((size_t)i * nv + jv) * nu + ju;
-            r = __ldg(b + idx) - acc * dlh;
-            if (!WEIGHTED) {
+            float r = __ldg(b + idx) - acc * dlh;
+            if (WEIGHTED) {
+                out[idx] = from_f32<OT>(r * dlh);
+                s[0] = (double)r * (double)r;
+            } else {
                 OT ro = from_f32<OT>(r);
                 out[idx] = ro;
                 float rf = to_f32(ro);
                 s[0] = (double)rf * (double)rf;
-            } else {
-                s[0] = (double)r * (double)r;
             }
-        }
-        if (WEIGHTED) {
-            __shared__ float tile[PJ_BX][PJ_BY + 1];
-            tile[threadIdx.x][threadIdx.y] = r * dlh;
-            __syncthreads();
-            const int t = threadIdx.x + threadIdx.y * PJ_BX;
-            const int tu = t / PJ_BY, tv = t % PJ_BY;
-            int u0, v0;
-            tile_origin(nv, u0, v0);
-            if (u0 + tu < nu && v0 + tv < nv && active_view(i))
-                out[colmajor_index(i, u0 + tu, v0 + tv, nu, nv)] = from_f32<OT>(tile[tu][tv]);
         }
         if (part) {
             __shared__ double red[PJ_BX * PJ_BY / 32];
@@ -249,11 +224,10 @@ struct EpiResidual {
             if (threadIdx.x == 0 && threadIdx.y == 0) part[block_linear()] = s[0];
         }
     }
-    __device__ bool active_view(int i) const { return i < nviews; }
 };
 
 // Line-search dot products per block, no sinogram write:
-//   <r, A d> = sum r_w * acc  (r_w = r * dlh, the weighted residual, [i][u][v])
+//   <r, A d> = sum r_w * acc  (r_w = r * dlh, the weighted residual)
 //   |A d|^2  = sum (acc * dlh)^2
 template <typename RT>
 struct EpiDualDot {
@@ -261,20 +235,9 @@ struct EpiDualDot {
     double *part;  // [blocks][2]
     int nu, nv, nviews;
     __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
-        __shared__ float tile[PJ_BX][PJ_BY + 1];
-        {
-            const int t = threadIdx.x + threadIdx.y * PJ_BX;
-            const int tu = t / PJ_BY, tv = t % PJ_BY;
-            int u0, v0;
-            tile_origin(nv, u0, v0);
-            float v = 0.0f;
-            if (i < nviews && u0 + tu < nu && v0 + tv < nv) v = to_f32(rw[colmajor_index(i, u0 + tu, v0 + tv, nu, nv)]);
-            tile[tu][tv] = v;
-        }
-        __syncthreads();
         double s[2] = {0.0, 0.0};
         if (active) {
-            float rv = tile[threadIdx.x][threadIdx.y];
+            float rv = to_f32(rw[((size_t)i * nv + jv) * nu + ju]);
             float ad = acc * dlh;
             s[0] = (double)rv * (double)acc;
             s[1] = (double)ad * (double)ad;
@@ -292,28 +255,21 @@ struct EpiDualDot {
 // OS-EMTR (Eq. 3) sinogram terms for one subset, weighted by dlh:
 //   t = exp(-A mu);  c0 = (t - exp(-b)) dlh  (I/I0 = exp(-b));  c1 = t PI dlh
 // b and PI are full [K][nv][nu] arrays indexed by the view k; c is a batch
-// two-channel sinogram [i][u][v][2].
+// two-channel sinogram [i][v][u][2].
 struct EpiEMTerms {
     float2 *c;
     const float *b;
     const float *pi;
     int nu, nv, nviews;
     __device__ void operator()(int i, int k, int jv, int ju, bool active, float acc, float dlh) const {
-        float2 o = make_float2(0.0f, 0.0f);
-        if (active) {
-            size_t full = ((size_t)k * nv + jv) * nu + ju;
-            float t = expf(-acc * dlh);
-            o.x = (t - expf(-__ldg(b + full))) * dlh;
-            o.y = t * __ldg(pi + full) * dlh;
-        }
-        __shared__ float2 tile[PJ_BX][PJ_BY + 1];
-        tile[threadIdx.x][threadIdx.y] = o;
-        __syncthreads();
-        const int t = threadIdx.x + threadIdx.y * PJ_BX;
-        const int tu = t / PJ_BY, tv = t % PJ_BY;
-        int u0, v0;
-        tile_origin(nv, u0, v0);
-        if (i < nviews && u0 + tu < nu && v0 + tv < nv) c[colmajor_index(i, u0 + tu, v0 + tv, nu, nv)] = tile[tu][tv];
+        if (!active) return;
+        size_t pix = (size_t)jv * nu + ju;
+        size_t full = (size_t)k * nv * nu + pix;
+        float t = expf(-acc * dlh);
+        float2 o;
+        o.x = (t - expf(-__ldg(b + full))) * dlh;
+        o.y = t * __ldg(pi + full) * dlh;
+        c[(size_t)i * nv * nu + pix] = o;
     }
 };
 

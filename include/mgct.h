@@ -181,6 +181,12 @@ typedef struct {
     double lambda;        /* soft-threshold level (Alg. 1 SoftThreshold); 0 = none */
     int32_t precondition; /* 1: d = p * B r (Eq. 4); 0: d = B r (SIRT, Eq. 2) */
     int32_t n_subsets;    /* OS-EMTR subsets M on the coarsest grid (multigrid only) */
+    int32_t storage;      /* mgct_dtype of the copies the projector and back-projector read:
+                             MGCT_F32, or MGCT_BF16 / MGCT_F16 for a 16-bit shadow of mu and
+                             of the search direction and a 16-bit residual sinogram; mu itself
+                             (the master copy), b, the filter and the update stay float32,
+                             accumulation is float32, alpha and the norms float64 */
+    int32_t reserved0;    /* must be 0 */
     const float *learned_corr; /* reserved, must be NULL */
 } mgct_lw_opts;
 

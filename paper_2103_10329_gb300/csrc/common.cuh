@@ -228,6 +228,8 @@ inline size_t project_blocks(int nu, int nv, int nviews) {
 // ---------------------------------------------------------------------------
 template <typename T>
 int launch_transpose_xy(int n, const T *in, T *out, cudaStream_t s);
+template <typename T>
+int launch_cast_transpose(int n, const float *in, T *out, T *outT, cudaStream_t s);
 
 int launch_sum_partials(const double *part, int count, int nvals, double *out, cudaStream_t s);
 

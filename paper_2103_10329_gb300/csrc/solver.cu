@@ -5,6 +5,7 @@
 // step size is computed on the device and read there by the update kernel,
 // so an iteration issues no host synchronisation.
 #include <cstring>
+#include <type_traits>
 
 #include "backproject.cuh"
 #include "common.cuh"
@@ -139,41 +140,76 @@ static int check_ws(const mgct_geom *g, int op, int level, const void *ws, size_
 // ---------------------------------------------------------------------------
 // Solver steps
 // ---------------------------------------------------------------------------
-static int landweber(const mgct_geom *g, int level, float *mu, const float *b, void *ws,
-                     const mgct_lw_opts &o, mgct_lw_stats *stats_out, cudaStream_t s) {
+// ST: storage type of the copies the projector and back-projector read (the
+// shadow of mu, the residual sinogram, the shadow of the search direction).
+template <typename ST>
+static int landweber_t(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
+                       mgct_lw_stats *stats_out, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
     Carver c(ws);
     LWSpace w = carve_lw(g, level, c);
     const int K = g->desc.n_views;
     const size_t nv3 = vox(L);
     double *stats = stats_out ? reinterpret_cast<double *>(stats_out) : w.stats;
+    constexpr bool F32 = std::is_same<ST, float>::value;
     MGCT_TRY(check_cuda(cudaMemsetAsync(w.sums, 0, 8 * sizeof(double), s), "memset"));
-    // r = b - A mu, |r|^2
-    MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
+    // projector inputs: mu itself (+ x-major copy), or 16-bit shadows of both
+    const ST *muS;
+    const ST *muST;
+    if constexpr (F32) {
+        MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
+        muS = mu;
+        muST = w.muT;
+    } else {
+        ST *a = reinterpret_cast<ST *>(w.muT);
+        MGCT_TRY(launch_cast_transpose<ST>(L.n, mu, a, a + nv3, s));
+        muS = a;
+        muST = a + nv3;
+    }
+    // r = b - A mu, stored weighted by each ray's dl; |r|^2 in float64
+    ST *r = reinterpret_cast<ST *>(w.r);
     int nb = 0;
-    // r is stored weighted by each ray's dl, which the back-projector then skips
-    EpiResidual<float, true> er{w.r, b, w.part, L.nu, L.nv, K};
-    MGCT_TRY(launch_project<float>(g, level, 0, K, 1, mu, w.muT, er, s, &nb));
+    EpiResidual<ST, true> er{r, b, w.part, L.nu, L.nv, K};
+    MGCT_TRY(launch_project<ST>(g, level, 0, K, 1, muS, muST, er, s, &nb));
     MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
-    // d = p * A^T r   (or A^T r for SIRT)
-    MGCT_TRY(launch_backproject<1, float, true>(g, level, 0, K, 1, w.r, w.grad, 0, s));
-    float *d = w.grad, *dT = w.d;
+    // d = p * A^T r   (or A^T r for SIRT), float32
+    MGCT_TRY(launch_backproject<1, ST, true>(g, level, 0, K, 1, r, w.grad, 0, s));
+    float *d = w.grad, *spare = w.d;
     if (o.precondition) {
         MGCT_TRY(launch_precondition(L.n, g->desc.p_slice_axis, w.grad, w.d, s));
         d = w.d;
-        dT = w.grad;  // the gradient is no longer needed
+        spare = w.grad;  // the gradient is no longer needed
     }
     if (!(o.alpha > 0.0)) {
         // exact line search along d: <r, A d>, |A d|^2
-        MGCT_TRY(launch_transpose_xy<float>(L.n, d, dT, s));
-        EpiDualDot<float> ed{w.r, w.part, L.nu, L.nv, K};
-        MGCT_TRY(launch_project<float>(g, level, 0, K, 1, d, dT, ed, s, &nb));
+        const ST *dS;
+        const ST *dST;
+        if constexpr (F32) {
+            MGCT_TRY(launch_transpose_xy<float>(L.n, d, spare, s));
+            dS = d;
+            dST = spare;
+        } else {
+            ST *a = reinterpret_cast<ST *>(spare);
+            MGCT_TRY(launch_cast_transpose<ST>(L.n, d, a, a + nv3, s));
+            dS = a;
+            dST = a + nv3;
+        }
+        EpiDualDot<ST> ed{r, w.part, L.nu, L.nv, K};
+        MGCT_TRY(launch_project<ST>(g, level, 0, K, 1, dS, dST, ed, s, &nb));
         MGCT_TRY(launch_sum_partials(w.part, nb, 2, w.sums + 1, s));
     }
     MGCT_TRY(launch_step_size(w.sums + 1, w.sums + 0, o.alpha > 0.0 ? o.alpha : 0.0, stats, s));
     MGCT_TRY(launch_update(nv3, mu, d, stats, (float)o.lambda, s));
-    (void)nv3;
     return MGCT_OK;
+}
+
+static int landweber(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
+                     mgct_lw_stats *stats_out, cudaStream_t s) {
+    switch (o.storage) {
+        case MGCT_BF16: return landweber_t<__nv_bfloat16>(g, level, mu, b, ws, o, stats_out, s);
+        case MGCT_F16: return landweber_t<__half>(g, level, mu, b, ws, o, stats_out, s);
+        default: return landweber_t<float>(g, level, mu, b, ws, o, stats_out, s);
+    }
 }
 
 static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *b, const float *pi, void *ws,
@@ -220,6 +256,8 @@ static int check_opts(const mgct_lw_opts *o) {
     if (o->learned_corr) return set_error(MGCT_EINVAL, "learned_corr is reserved and must be NULL");
     if (!(o->lambda >= 0.0)) return set_error(MGCT_EINVAL, "lambda must be >= 0");
     if (o->n_subsets < 0) return set_error(MGCT_EINVAL, "n_subsets must be >= 0");
+    if (o->storage < MGCT_F32 || o->storage > MGCT_F16 || o->reserved0 != 0)
+        return set_error(MGCT_EINVAL, "storage must be MGCT_F32, MGCT_BF16 or MGCT_F16 (reserved0 = 0)");
     return MGCT_OK;
 }
 

@@ -36,6 +36,7 @@ class GeomDesc(ctypes.Structure):
 class LwOpts(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("precondition", ctypes.c_int32), ("n_subsets", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("learned_corr", ctypes.c_void_p)]
 
 
@@ -262,19 +263,20 @@ def workspace(geom: Geometry, op: int, level: int = 0, device="cuda") -> torch.T
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
-def _opts(alpha, lam, precond, n_subsets):
+def _opts(alpha, lam, precond, n_subsets, storage=torch.float32):
     return LwOpts(float(alpha) if alpha is not None else 0.0, float(lam), 1 if precond else 0,
-                  int(n_subsets), None)
+                  int(n_subsets), _DT[storage], 0, None)
 
 
 def landweber_step(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, level: int = 0, alpha=None,
                    lam: float = 0.0, precond: bool = True, ws: torch.Tensor | None = None,
-                   stats: torch.Tensor | None = None):
+                   stats: torch.Tensor | None = None, storage=torch.float32):
     """One (preconditioned) Landweber step in place; stats: float64[4] device
-    tensor (alpha, r2, r2_pred, nonfinite) or None."""
+    tensor (alpha, r2, r2_pred, nonfinite) or None; storage: dtype of the
+    copies the projector and back-projector read (float32, bfloat16, float16)."""
     if ws is None:
         ws = workspace(geom, WS_LANDWEBER, level, vol.device)
-    o = _opts(alpha, lam, precond, 0)
+    o = _opts(alpha, lam, precond, 0, storage)
     _check(lib().mgct_landweber_step(geom.handle, level, _ptr(vol, "vol", torch.float32),
                                      _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(), ctypes.byref(o),
                                      _ptr(stats, "stats", torch.float64), _stream()))
@@ -298,8 +300,8 @@ def multigrid_prepare(geom: Geometry, b: torch.Tensor, ws: torch.Tensor):
 
 def multigrid_iteration(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, ws: torch.Tensor, alpha=None,
                         lam: float = 0.0, precond: bool = True, n_subsets: int = 8,
-                        stats: torch.Tensor | None = None):
-    o = _opts(alpha, lam, precond, n_subsets)
+                        stats: torch.Tensor | None = None, storage=torch.float32):
+    o = _opts(alpha, lam, precond, n_subsets, storage)
     _check(lib().mgct_multigrid_iteration(geom.handle, _ptr(vol, "vol", torch.float32),
                                           _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(),
                                           ctypes.byref(o), _ptr(stats, "stats", torch.float64), _stream()))

@@ -232,6 +232,18 @@ int mgct_multigrid_iteration(const mgct_geom *geom, float *vol, const float *b, 
                              mgct_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Geometry gradient (Sec. 1: drift of the source and detector, estimated
+ * jointly with the image).  dphi[i][5] = d/dphi of sum_rays y * (A vol) over
+ * the rays of view view0 + i * view_stride, for phi = (ds_u, ds_v, dd_u,
+ * dd_v [fine pixels], psi [rad]) of that view (the drift of
+ * mgct_geometry_desc), at fixed major axis and plane set (A is piecewise
+ * smooth in phi).  vol: float32 [n_g]^3; y: float32 batch sinogram; dphi:
+ * device double [nviews * 5], overwritten.  Uses the handle's scratch.
+ * ------------------------------------------------------------------------- */
+int mgct_geometry_grad(const mgct_geom *geom, int level, int view0, int nviews, int view_stride,
+                       const float *vol, const float *y, double *dphi, mgct_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Residual projection without any device allocation.  The paper has no
  * counterpart: this is a library service.
  *

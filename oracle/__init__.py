@@ -75,6 +75,7 @@ def _load():
         lib.orc_weight.restype = ctypes.c_double
         lib.orc_backproject_voxels.argtypes = [i, i, i, i, dp, dp, dp, dp, dp, i, ip, i, dp, ip]
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_project_grad.argtypes = [i, i, i, i, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         _lib = lib
     return _lib
 
@@ -233,6 +234,46 @@ def weight(g: LevelGeom, view: int, ju: int, jv: int, ix: int, iy: int, iz: int)
     """One entry of A, from the definition (independent of the plane loop)."""
     return _load().orc_weight(g.n, _dp(g.src[view]), _dp(g.det[view]), _dp(g.pu[view]),
                               _dp(g.pv[view]), ju, jv, ix, iy, iz)
+
+
+# ----------------------------------------------------------------------------
+# Per-view geometry gradient (Sec. 1: drift estimated jointly with the image)
+# ----------------------------------------------------------------------------
+
+def nominal_axes(scan: Scan):
+    """Untilted detector axes e_u, e_v [K,3] along which the drift offsets act."""
+    th = np.asarray(scan.theta, dtype=np.float64)
+    zero = np.zeros_like(th)
+    return (np.stack([-np.sin(th), np.cos(th), zero], axis=1),
+            np.stack([zero, zero, np.ones_like(th)], axis=1))
+
+
+def geometry_grad(scan: Scan, vol: np.ndarray, y: np.ndarray, level: int = 0) -> np.ndarray:
+    """d/d phi_k of sum_rays y * (P mu)_ray for phi_k = (ds_u, ds_v, dd_u, dd_v,
+    psi): the ray end-point derivatives of joseph.c chained through the
+    geometry: ds_u, ds_v move the source by pitch e_u, pitch e_v; dd_u, dd_v
+    move every pixel the same way; psi turns the pixel offsets (u' e_u' +
+    v' e_v') pitch_g about the detector normal, d/dpsi = u' e_v' - v' e_u'.
+    Returns [K, 5]."""
+    g = level_geometry(scan, level)
+    vol = np.ascontiguousarray(vol, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    K = g.n_views
+    gs, gp, gpu, gpv = (np.zeros((K, 3)) for _ in range(4))
+    rc = _load().orc_project_grad(g.n, g.nu, g.nv, K, _dp(g.src), _dp(g.det), _dp(g.pu), _dp(g.pv), _dp(vol),
+                                  _dp(y), _dp(gs), _dp(gp), _dp(gpu), _dp(gpv))
+    if rc != 0:
+        raise ValueError("z-major ray")
+    eu, ev = nominal_axes(scan)
+    p0 = scan.pitch
+    out = np.zeros((K, 5))
+    out[:, 0] = p0 * np.sum(gs * eu, axis=1)
+    out[:, 1] = p0 * np.sum(gs * ev, axis=1)
+    out[:, 2] = p0 * np.sum(gp * eu, axis=1)
+    out[:, 3] = p0 * np.sum(gp * ev, axis=1)
+    # pu, pv are the tilted pixel steps (pitch_g e_u', pitch_g e_v')
+    out[:, 4] = np.sum(gpu * g.pv, axis=1) - np.sum(gpv * g.pu, axis=1)
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -321,3 +321,107 @@ int orc_backproject_voxels(int n, int nu, int nv, int nviews,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Derivative of the line integrals with respect to the ray end points, for
+ * the per-view geometry gradient (joint estimation of drift, Sec. 1).
+ *
+ * For a ray from s to the pixel centre p (w = p - s), Joseph's integral is
+ * I = dl * sum_i B(f_b(i), f_c(i)), dl = h |w| / |w_a|, with the crossing of
+ * plane c_i: t_i = (c_i - s_a) / w_a, x = s + t_i w, f = x / h + (N-1)/2.
+ * Differentiating at fixed major axis a and fixed plane set:
+ *   dt/ds_a = (c - p_a) / w_a^2,   dt/dp_a = -t / w_a,
+ *   dx_q/ds_q = 1 - t, dx_q/dp_q = t (q != a), dx_q/d(s_a, p_a) = w_q dt/d(.),
+ *   d dl / dw_j = h (w_j / (|w| |w_a|) - [j = a] |w| sign(w_a) / w_a^2),
+ * and B's gradient is that of the bilinear interpolant (zero padding).
+ * Per view it returns sums weighted by the cotangent y:
+ *   gs[k][3]  = sum y dI/ds,          gp[k][3]  = sum y dI/dp,
+ *   gpu[k][3] = sum y dI/dp * ju',    gpv[k][3] = sum y dI/dp * jv',
+ * with ju' = ju - (nu-1)/2, jv' = jv - (nv-1)/2 (centred pixel indices).
+ * ------------------------------------------------------------------------ */
+static void ray_grad(const ray_t *r, int n, double h, const double *vol, double *dI_ds, double *dI_dp)
+{
+    const double half = 0.5 * (n - 1);
+    const int a = r->a, b = r->b, c = r->c;
+    const double wa = r->w[a];
+    double nw = sqrt(r->w[0] * r->w[0] + r->w[1] * r->w[1] + r->w[2] * r->w[2]);
+    double sum = 0.0;
+    double g_s[3] = {0, 0, 0}, g_p[3] = {0, 0, 0};
+    for (int ia = 0; ia < n; ++ia) {
+        double cpos = (ia - half) * h;
+        double t = (cpos - r->s[a]) / wa;
+        double xb = r->s[b] + t * r->w[b], xc = r->s[c] + t * r->w[c];
+        double fb = xb / h + half, fc = xc / h + half;
+        double fb0 = floor(fb), fc0 = floor(fc);
+        double tb = fb - fb0, tc = fc - fc0;
+        int ib = (int)fb0, ic = (int)fc0;
+        double v[2][2];
+        for (int db = 0; db < 2; ++db)
+            for (int dc = 0; dc < 2; ++dc) {
+                int jb = ib + db, jc = ic + dc;
+                v[db][dc] = (jb >= 0 && jb < n && jc >= 0 && jc < n)
+                                ? vol[vox_index(n, a, b, c, ia, jb, jc)] : 0.0;
+            }
+        double val = (1 - tb) * (1 - tc) * v[0][0] + tb * (1 - tc) * v[1][0]
+                   + (1 - tb) * tc * v[0][1] + tb * tc * v[1][1];
+        double dB_dfb = (1 - tc) * (v[1][0] - v[0][0]) + tc * (v[1][1] - v[0][1]);
+        double dB_dfc = (1 - tb) * (v[0][1] - v[0][0]) + tb * (v[1][1] - v[1][0]);
+        sum += val;
+        double dt_dsa = (cpos - (r->s[a] + wa)) / (wa * wa);  /* (c - p_a) / w_a^2 */
+        double dt_dpa = -t / wa;
+        /* dx_b, dx_c with respect to s and p */
+        g_s[b] += dB_dfb / h * (1 - t);
+        g_p[b] += dB_dfb / h * t;
+        g_s[c] += dB_dfc / h * (1 - t);
+        g_p[c] += dB_dfc / h * t;
+        g_s[a] += (dB_dfb * r->w[b] + dB_dfc * r->w[c]) / h * dt_dsa;
+        g_p[a] += (dB_dfb * r->w[b] + dB_dfc * r->w[c]) / h * dt_dpa;
+    }
+    double dl = h * nw / fabs(wa);
+    for (int j = 0; j < 3; ++j) {
+        double ddl_dw = h * (r->w[j] / (nw * fabs(wa)));
+        if (j == a) ddl_dw -= h * nw * (wa > 0 ? 1.0 : -1.0) / (wa * wa);
+        /* w = p - s */
+        dI_dp[j] = ddl_dw * sum + dl * g_p[j];
+        dI_ds[j] = -ddl_dw * sum + dl * g_s[j];
+    }
+}
+
+int orc_project_grad(int n, int nu, int nv, int nviews, const double *src, const double *det,
+                     const double *pu, const double *pv, const double *vol, const double *y,
+                     double *gs, double *gp, double *gpu, double *gpv)
+{
+    double h = 1.0 / n;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int k = 0; k < nviews; ++k) {
+        double as[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, apu[3] = {0, 0, 0}, apv[3] = {0, 0, 0};
+        for (int jv = 0; jv < nv; ++jv) {
+            for (int ju = 0; ju < nu; ++ju) {
+                double yy = y[((size_t)k * nv + jv) * nu + ju];
+                if (yy == 0.0) continue;
+                ray_t r;
+                if (make_ray(src + 3 * k, det + 3 * k, pu + 3 * k, pv + 3 * k, ju, jv, h, &r)) {
+                    bad = 1;
+                    continue;
+                }
+                double ds[3], dp[3];
+                ray_grad(&r, n, h, vol, ds, dp);
+                double uc = ju - 0.5 * (nu - 1), vc = jv - 0.5 * (nv - 1);
+                for (int j = 0; j < 3; ++j) {
+                    as[j] += yy * ds[j];
+                    ap[j] += yy * dp[j];
+                    apu[j] += yy * dp[j] * uc;
+                    apv[j] += yy * dp[j] * vc;
+                }
+            }
+        }
+        for (int j = 0; j < 3; ++j) {
+            gs[3 * k + j] = as[j];
+            gp[3 * k + j] = ap[j];
+            gpu[3 * k + j] = apu[j];
+            gpv[3 * k + j] = apv[j];
+        }
+    }
+    return bad ? -1 : 0;
+}

@@ -50,7 +50,9 @@ struct ViewGeom {
     float Ev_lo[3];
     float NX_lo[6];
     float NY_lo[6];
-    float pad1[7];
+    float Du[3];  // drift directions (index units of this grid): one fine pixel
+    float Dv[3];  // along the untilted detector axes e_u, e_v
+    float pad1;
 };
 static_assert(sizeof(ViewGeom) == 256, "ViewGeom layout");
 

@@ -81,6 +81,7 @@ static int build_view(const mgct_geom *g, int level, int k, ViewGeom *out, std::
     double th = g->theta[k];
     double c = std::cos(th), s = std::sin(th);
     V3 eu = {-s, c, 0.0}, ev = {0.0, 0.0, 1.0}, nrm = {-c, -s, 0.0};
+    const V3 eu_nom = eu, ev_nom = ev;
     V3 base = {d.src_axis_dist * c, d.src_axis_dist * s, g->z[k]};
     V3 src = base;
     V3 dcen = add(base, mul(d.src_det_dist, nrm));
@@ -159,6 +160,13 @@ static int build_view(const mgct_geom *g, int level, int k, ViewGeom *out, std::
     }
     for (int i = 0; i < 9; ++i) out->Q[i] = (float)q[i];
     out->m2 = (float)m2;
+    const V3 du = mul(d.pixel_pitch / h, eu_nom), dv = mul(d.pixel_pitch / h, ev_nom);
+    out->Du[0] = (float)du.x;
+    out->Du[1] = (float)du.y;
+    out->Du[2] = (float)du.z;
+    out->Dv[0] = (float)dv.x;
+    out->Dv[1] = (float)dv.y;
+    out->Dv[2] = (float)dv.z;
     // crossing numerators with the central plane of the major axis a:
     // P_b = (s'_b w_a - s'_a w_b) / w_a with s' = S - ic, expanded in (u', v')
     const double sc[3] = {S.x - half, S.y - half, S.z - half};
@@ -302,7 +310,9 @@ int mgct_geometry_create(const mgct_geom_desc *d, mgct_geom **out) {
     // partials: one per projector block (32 x 8 pixels per view), two values each
     size_t blocks = project_blocks(d->nu, d->nv, K);
     size_t vblocks = (nvox + 255) / 256;
+    size_t gblocks = 5 * (size_t)K * ((d->nu + PJ_BX - 1) / PJ_BX);  // geometry-gradient partials
     g->scratch_part_count = 2 * (blocks > vblocks ? blocks : vblocks) + 64;
+    if (gblocks > g->scratch_part_count) g->scratch_part_count = gblocks;
     st = check_cuda(cudaMalloc(&g->d_scratch_vol, nvox * 4), "allocate scratch volume");
     if (!st) st = check_cuda(cudaMalloc(&g->d_scratch_part, g->scratch_part_count * sizeof(double)),
                              "allocate scratch partials");

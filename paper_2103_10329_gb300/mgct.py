@@ -76,6 +76,8 @@ def lib():
     L.mgct_launch_count.restype = ctypes.c_uint64
     L.mgct_trace_enable.argtypes = [i]
     L.mgct_trace_read.argtypes = [vp, vp, i]
+    L.mgct_geometry_grad.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
+    L.mgct_geometry_grad.restype = ctypes.c_int
     L.mgct_project_residual_static.argtypes = [vp, i, i, i, i, vp, vp, vp, vp, vp]
     L.mgct_project_residual_static.restype = ctypes.c_int
     L.mgct_project_residual_static_bytes.restype = sz
@@ -222,6 +224,16 @@ def backproject(geom: Geometry, sino: torch.Tensor, level: int = 0, views=None, 
         out = torch.empty((n, n, n), device=sino.device, dtype=torch.float32)
     _check(lib().mgct_backproject(geom.handle, level, v0, cnt, stride, _ptr(sino, "sino"), _DT[sino.dtype],
                                   _ptr(out, "out", torch.float32), 1 if accumulate else 0, _stream()))
+    return out
+
+
+def geometry_grad(geom: Geometry, vol: torch.Tensor, y: torch.Tensor, level: int = 0, views=None, out=None):
+    """d/dphi of sum y * (A vol) per view, phi = (ds_u, ds_v, dd_u, dd_v, psi): float64 [nviews, 5]."""
+    v0, cnt, stride = _views(geom, views)
+    if out is None:
+        out = torch.empty((cnt, 5), device=vol.device, dtype=torch.float64)
+    _check(lib().mgct_geometry_grad(geom.handle, level, v0, cnt, stride, _ptr(vol, "vol", torch.float32),
+                                    _ptr(y, "y", torch.float32), _ptr(out, "out", torch.float64), _stream()))
     return out
 
 

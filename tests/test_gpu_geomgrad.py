@@ -1,0 +1,131 @@
+"""Differentiable form: the per-view geometry gradient kernel and the autograd
+wrappers, against the FP64 oracle's analytic gradient (itself pinned by
+central differences and by the closed-form Gaussian line integral)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2103_10329_gb300 import synth
+from tests.helpers import cuda, gpu_geom, oracle_scan, scan_desc, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2103_10329_gb300 import build
+    build.build()
+    O.build()
+
+
+def smooth_volume(n, seed=5):
+    return synth.voxelize_blobs(synth.blobs(4, seed, 0.06, 0.12, centre_r=0.2), n).numpy()
+
+
+@pytest.mark.parametrize("tilt", [False, True])
+def test_geometry_grad_vs_oracle(tilt):
+    from paper_2103_10329_gb300 import mgct
+    K, n, nu = 12, 40, 60
+    drift = synth.drift_walk(K, 8, sigma_px=0.6, half_diag_px=40)
+    if not tilt:
+        drift[:, 4] = 0.0
+    d = scan_desc(n, nu, nu, K, 2104, levels=1, drift=drift)
+    g = gpu_geom(d)
+    vol = smooth_volume(n)
+    y = np.random.default_rng(3).standard_normal((K, nu, nu))
+    ref = O.geometry_grad(oracle_scan(d), vol.astype(np.float32).astype(np.float64),
+                          y.astype(np.float32).astype(np.float64))
+    got = to_np(mgct.geometry_grad(g, cuda(vol), cuda(y)))
+    err = np.abs(got - ref)
+    # per parameter type, relative to that type's largest entry
+    for j in range(5):
+        assert err[:, j].max() <= 2e-4 * np.abs(ref[:, j]).max(), (j, err[:, j].max(), np.abs(ref[:, j]).max())
+
+
+def test_view_subset_gradient():
+    from paper_2103_10329_gb300 import mgct
+    K, n, nu = 16, 32, 48
+    drift = synth.drift_walk(K, 9, sigma_px=0.4, half_diag_px=30)
+    d = scan_desc(n, nu, nu, K, 2104, levels=1, drift=drift)
+    g = gpu_geom(d)
+    vol = cuda(smooth_volume(n))
+    y = cuda(np.random.default_rng(4).standard_normal((K, nu, nu)))
+    full = mgct.geometry_grad(g, vol, y)
+    sub = mgct.geometry_grad(g, vol, y[1::3].contiguous(), views=(1, len(range(1, K, 3)), 3))
+    assert torch.allclose(sub, full[1::3], rtol=1e-12, atol=0)
+
+
+def test_autograd_project_matches_oracle():
+    from paper_2103_10329_gb300 import autograd as AG
+    K, n, nu = 10, 32, 48
+    drift = synth.drift_walk(K, 10, sigma_px=0.5, half_diag_px=30)
+    d = scan_desc(n, nu, nu, K, 2104, levels=1, drift=drift)
+    g = gpu_geom(d)
+    vol_np = smooth_volume(n)
+    y_np = np.random.default_rng(6).standard_normal((K, nu, nu)).astype(np.float32)
+    vol = cuda(vol_np).requires_grad_(True)
+    phi = torch.tensor(drift, dtype=torch.float64, device="cuda", requires_grad=True)
+    loss = (AG.project(vol, g, phi) * cuda(y_np)).sum()
+    loss.backward()
+    og = O.level_geometry(oracle_scan(d), 0)
+    ref_vol = O.backproject(og, y_np.astype(np.float64))
+    ref_phi = O.geometry_grad(oracle_scan(d), vol_np.astype(np.float32).astype(np.float64), y_np.astype(np.float64))
+    gv = to_np(vol.grad)
+    assert np.abs(gv - ref_vol).max() <= 1e-5 * np.abs(ref_vol).max() * 10
+    gp = phi.grad.cpu().numpy()
+    for j in range(5):
+        assert np.abs(gp[:, j] - ref_phi[:, j]).max() <= 2e-4 * np.abs(ref_phi[:, j]).max()
+    # the backward of the back-projection is the projection
+    yy = cuda(y_np).requires_grad_(True)
+    w = cuda(vol_np)
+    (AG.backproject(yy, g) * w).sum().backward()
+    ref_y = O.project(og, vol_np.astype(np.float32).astype(np.float64))
+    assert np.abs(to_np(yy.grad) - ref_y).max() <= 1e-5 * np.abs(ref_y).max() * 10
+
+
+def test_joint_estimation_recovers_detector_offset():
+    """Sec. 1 motivates estimating drift jointly with the image.  Data made
+    with every view's detector shifted by 1.5 pixels along u; starting from no
+    drift, alternating multigrid iterations on mu with gradient steps on a
+    shared offset through the autograd projector recovers the shift."""
+    from paper_2103_10329_gb300 import autograd as AG
+    from paper_2103_10329_gb300 import mgct
+    K, n, nu = 40, 32, 48
+    true = np.zeros((K, 5))
+    true[:, 2] = 1.5
+    d_true = scan_desc(n, nu, nu, K, 2104, levels=2, drift=true)
+    truth = smooth_volume(n, seed=11)
+    b = cuda(O.project(O.level_geometry(oracle_scan(d_true), 0), truth))
+    g = gpu_geom(scan_desc(n, nu, nu, K, 2104, levels=2))
+    rec = mgct.Reconstructor(g)
+    off = 0.0
+    vol = torch.zeros((n, n, n), device="cuda")
+    errs = []
+    for outer in range(6):
+        phi_np = np.zeros((K, 5))
+        phi_np[:, 2] = off
+        g.set_drift(phi_np)
+        rec.prepare(b)
+        for _ in range(2):
+            rec.iterate(vol)
+        for _ in range(3):
+            phi = torch.tensor(phi_np, device="cuda", requires_grad=True)
+            r = AG.project(vol, g, phi) - b
+            loss = 0.5 * (r * r).sum()
+            loss.backward()
+            gsum = float(phi.grad[:, 2].sum())
+            # Gauss-Newton step on the shared offset: curvature from a secant
+            eps = 0.05
+            p2 = phi_np.copy()
+            p2[:, 2] += eps
+            phi2 = torch.tensor(p2, device="cuda", requires_grad=True)
+            r2 = AG.project(vol, g, phi2) - b
+            (0.5 * (r2 * r2).sum()).backward()
+            curv = (float(phi2.grad[:, 2].sum()) - gsum) / eps
+            if curv > 0:
+                off -= gsum / curv
+            phi_np[:, 2] = off
+        errs.append(abs(off - 1.5))
+    assert errs[-1] < 0.2 * 1.5, errs
+    assert errs[-1] < errs[0], errs

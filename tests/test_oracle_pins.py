@@ -438,3 +438,62 @@ def test_pmgl_beats_sirt_at_equal_cost():
     e_mg = np.sqrt(np.mean((mg - truth) ** 2))
     e_sirt = np.sqrt(np.mean((sirt - truth) ** 2))
     assert e_mg < e_sirt, (e_mg, e_sirt)
+
+
+# ---------------------------------------------------------------- geometry gradient
+
+def _grad_scan(drift, n=20, nu=30, nviews=4):
+    th, z = synth.trajectory(nviews, 3)
+    return O.Scan(n=n, nu=nu, nv=nu, theta=th, z=0.3 * z, pitch=synth.default_pitch(nu), drift=drift)
+
+
+def test_geometry_grad_matches_central_differences():
+    """The analytic end-point derivative chained to phi equals central
+    differences of the oracle's own P (step 1e-6 px: below the spacing of the
+    bilinear interpolant's kinks, so the integral is locally smooth)."""
+    K = 4
+    drift = synth.drift_walk(K, 4, sigma_px=0.5, half_diag_px=20)
+    ph = synth.blobs(3, 5, 0.08, 0.12, centre_r=0.15)
+    vol = synth.voxelize_blobs(ph, 20).numpy()
+    y = np.random.default_rng(0).standard_normal((K, 30, 30))
+    gr = O.geometry_grad(_grad_scan(drift), vol, y)
+    for k in range(K):
+        for j in range(5):
+            e = 1e-6 if j < 4 else 4e-8
+            d1, d2 = drift.copy(), drift.copy()
+            d1[k, j] += e
+            d2[k, j] -= e
+            a1 = O.project(O.level_geometry(_grad_scan(d1), 0), vol)[k]
+            a2 = O.project(O.level_geometry(_grad_scan(d2), 0), vol)[k]
+            fd = np.sum(y[k] * (a1 - a2)) / (2 * e)
+            assert abs(gr[k, j] - fd) <= 1e-6 * max(abs(fd), np.abs(gr).max()), (k, j, gr[k, j], fd)
+
+
+def test_geometry_grad_against_closed_form_blob():
+    """Independent of Joseph: the drift derivative of the closed-form Gaussian
+    line integral (central differences of the exact integral) against the
+    oracle's gradient on the sampled blob; agreement to the discretisation
+    error (measured 4.8 %, 2.2 %, 0.3 % of the largest entry at n = 20, 40, 80)."""
+    K = 3
+    drift = np.zeros((K, 5))
+    drift[:, 4] = 0.02
+    ph = synth.blobs(1, 9, 0.1, 0.1, centre_r=0.1)
+    n = 48
+    vol = synth.voxelize_blobs(ph, n).numpy()
+    scan = _grad_scan(drift, n=n, nu=60, nviews=K)
+    # weights = a ramp across the detector, so the derivatives are first
+    # moments of the projection (a constant weight would nearly cancel them)
+    uc = np.arange(60) - 29.5
+    y = np.broadcast_to(1.0 + 0.05 * uc[None, None, :] + 0.03 * uc[None, :, None], (K, 60, 60)).copy()
+    gr = O.geometry_grad(scan, vol, y)
+    for j in range(5):
+        e = 1e-4 if j < 4 else 4e-6
+        d1, d2 = drift.copy(), drift.copy()
+        d1[:, j] += e
+        d2[:, j] -= e
+        s1 = _grad_scan(d1, n=n, nu=60, nviews=K)
+        s2 = _grad_scan(d2, n=n, nu=60, nviews=K)
+        fd = (np.sum(y * O.blob_line_integrals(O.level_geometry(s1, 0), ph), axis=(1, 2))
+              - np.sum(y * O.blob_line_integrals(O.level_geometry(s2, 0), ph), axis=(1, 2))) / (2 * e)
+        scale = max(np.abs(fd).max(), 1e-3 * np.abs(gr).max())
+        assert np.abs(gr[:, j] - fd).max() <= 0.03 * scale, (j, gr[:, j], fd)

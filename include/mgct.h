@@ -244,6 +244,46 @@ int mgct_geometry_grad(const mgct_geom *geom, int level, int view0, int nviews, 
                        const float *vol, const float *y, double *dphi, mgct_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned preconditioner correction (Sec. 3 discussion: a more effective
+ * preconditioning kernel than Eq. 5 is wanted; this network learns a
+ * correction on top of it).
+ *
+ * Network f: four 3x3x3 convolutions at full resolution (zero padding),
+ * 1 -> 16 -> 32 -> 64 -> 1 channels, ReLU after the first three, on BF16
+ * tensor cores with float32 accumulation and BF16 activations; float32
+ * master weights trained by Adam.  Volumes are [B][D][H][W] float32, B
+ * volumes of D x H x W voxels, B*D*H*W < 2^31.
+ *
+ * mgct_net_apply: out = s (x + f(x)) with x = dir / s, s = RMS(dir): the
+ *   corrected step for the step dir (alpha d of a Landweber step).
+ * mgct_net_forward_backward: for scaled input x and target t, loss =
+ *   mean((x + f(x) - t)^2) into *loss (device double) and the gradients of
+ *   every parameter into the net (mgct_net_get_grads reads them).
+ * mgct_net_adam_step: one Adam step (beta 0.9 / 0.999, eps 1e-8) with the
+ *   last gradients.
+ * Parameters are exchanged as float32, layer by layer: weights
+ * [27][cout][cin] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)) then biases [cout];
+ * mgct_net_param_count() values in all.  mgct_net_create initialises with
+ * He-normal weights from `seed`, zero biases and a zero output layer.
+ * Workspaces: mgct_net_workspace_bytes(B*D*H*W, training) bytes, 256-byte
+ * aligned.
+ * ------------------------------------------------------------------------- */
+typedef struct mgct_net mgct_net;
+int mgct_net_create(uint64_t seed, mgct_net **out);
+void mgct_net_destroy(mgct_net *net);
+size_t mgct_net_param_count(void);
+int mgct_net_set_params(mgct_net *net, const float *host, size_t count);
+int mgct_net_get_params(const mgct_net *net, float *host, size_t count);
+int mgct_net_get_grads(const mgct_net *net, float *host, size_t count);
+size_t mgct_net_workspace_bytes(int64_t nvox, int training);
+int mgct_net_apply(const mgct_net *net, int B, int D, int H, int W, const float *dir, float *out,
+                   void *workspace, size_t ws_bytes, mgct_stream stream);
+int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const float *x,
+                              const float *t, void *workspace, size_t ws_bytes, double *loss,
+                              mgct_stream stream);
+int mgct_net_adam_step(mgct_net *net, double lr, mgct_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Residual projection without any device allocation.  The paper has no
  * counterpart: this is a library service.
  *

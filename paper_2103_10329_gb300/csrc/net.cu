@@ -1,0 +1,533 @@
+// Learned preconditioner correction: a small 3D convolutional network applied
+// to the preconditioned Landweber step (the paper's Sec. 3 discussion asks
+// for more effective preconditioning kernels than Eq. 5; the network learns
+// a correction on top of it).  Architecture: four 3x3x3 convolutions at full
+// resolution with 16, 32 and 64 hidden channels (ReLU) and one linear output
+// channel; its input is the step alpha d scaled to unit RMS, x = alpha d / s,
+// and the corrected step is d' = s (x + f(x)).  Training minimises the mean
+// of (x + f(x) - t)^2 with t = e / s, e the error of the current estimate, by
+// Adam on float32 master weights; the convolutions run on BF16 tensor cores
+// with float32 accumulation and BF16 activations.
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "common.cuh"
+#include "conv3d.cuh"
+
+namespace mgct {
+
+// Layer shapes (padded to multiples of 16 channels): input 1 real channel,
+// output 1 real channel.
+constexpr int NL = 4;
+constexpr int LCIN[NL] = {16, 16, 32, 64};
+constexpr int LCOUT[NL] = {16, 32, 64, 16};
+constexpr int LCIN_REAL[NL] = {1, 16, 32, 64};
+constexpr int LCOUT_REAL[NL] = {16, 32, 64, 1};
+
+inline size_t wcount(int l) { return (size_t)27 * LCOUT[l] * LCIN[l]; }
+
+}  // namespace mgct
+
+struct mgct_net {
+    float *w[mgct::NL], *b[mgct::NL];      // float32 master weights [27][COUT][CIN], bias [COUT]
+    float *mw[mgct::NL], *vw[mgct::NL];    // Adam moments
+    float *mb[mgct::NL], *vb[mgct::NL];
+    float *gw[mgct::NL], *gb[mgct::NL];    // gradients of the last forward_backward
+    __nv_bfloat16 *wf[mgct::NL];           // bf16 forward weights
+    __nv_bfloat16 *wt[mgct::NL];           // bf16 backward-data weights [26 - tap][CIN][COUT]
+    double *loss;                          // device scalar of the last forward_backward
+    int64_t step;
+};
+
+namespace mgct {
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+__global__ void k_pack_weights(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wf,
+                               __nv_bfloat16 *__restrict__ wt, int cout, int cin) {
+    const int n = 27 * cout * cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % cin, co = (i / cin) % cout, tap = i / (cin * cout);
+        const __nv_bfloat16 v = __float2bfloat16_rn(w[i]);
+        wf[i] = v;
+        wt[((size_t)(26 - tap) * cin + ci) * cout + co] = v;
+    }
+}
+
+// x (float32 [nvox]) scaled by 1/s into channel 0 of a 16-channel bf16 tensor;
+// s = sqrt(sumsq / nvox) from a device scalar (or 1 when scale == NULL).
+__global__ void k_net_input(const float *__restrict__ x, const double *__restrict__ sumsq, int nvox,
+                            __nv_bfloat16 *__restrict__ x0, float *__restrict__ xs) {
+    const float inv = sumsq ? (float)(1.0 / fmax(sqrt(sumsq[0] / (double)nvox), 1e-30)) : 1.0f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nvox; p += gridDim.x * blockDim.x) {
+        const float v = x[p] * inv;
+        if (xs) xs[p] = v;
+        uint4 z = make_uint4(0, 0, 0, 0);
+        __nv_bfloat16 *e = reinterpret_cast<__nv_bfloat16 *>(&z);
+        e[0] = __float2bfloat16_rn(v);
+        uint4 *dst = reinterpret_cast<uint4 *>(x0 + (size_t)p * 16);
+        dst[0] = z;
+        dst[1] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+// out = s (x + y)  (the corrected step in the caller's units)
+__global__ void k_net_output(const float *__restrict__ x, const float *__restrict__ y, const double *__restrict__ sumsq,
+                             int nvox, float *__restrict__ out) {
+    const float s = (float)fmax(sqrt(sumsq[0] / (double)nvox), 1e-30);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nvox; p += gridDim.x * blockDim.x)
+        out[p] = s * (x[p] + y[p]);
+}
+
+// loss partials and the output gradient: r = x + y - t; dL/dy = 2 r / N
+__global__ void k_mse(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ t, int nvox,
+                      __nv_bfloat16 *__restrict__ gy, double *__restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    const float sc = 2.0f / (float)nvox;
+    const double inv_n = 1.0 / (double)nvox;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nvox; p += gridDim.x * blockDim.x) {
+        const float r = x[p] + y[p] - t[p];
+        s += (double)r * (double)r * inv_n;
+        uint4 z = make_uint4(0, 0, 0, 0);
+        __nv_bfloat16 *e = reinterpret_cast<__nv_bfloat16 *>(&z);
+        e[0] = __float2bfloat16_rn(sc * r);
+        uint4 *dst = reinterpret_cast<uint4 *>(gy + (size_t)p * 16);
+        dst[0] = z;
+        dst[1] = make_uint4(0, 0, 0, 0);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// per-block channel sums of a bf16 [nvox][C] tensor (bias gradients), in a
+// fixed order: thread t sums channel t % C over voxel lane t / C, then the
+// lanes of each channel are added in lane order.
+__global__ void k_channel_sums(const __nv_bfloat16 *__restrict__ g, int nvox, int C, float *__restrict__ part) {
+    __shared__ float sm[256];
+    const int lanes = blockDim.x / C;
+    const int c = threadIdx.x % C, ln = threadIdx.x / C;
+    float s = 0.0f;
+    if (ln < lanes)
+        for (int p = blockIdx.x * lanes + ln; p < nvox; p += gridDim.x * lanes) s += __bfloat162float(g[(size_t)p * C + c]);
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.0f;
+        for (int l = 0; l < lanes; ++l) t += sm[l * C + threadIdx.x];
+        part[(size_t)blockIdx.x * C + threadIdx.x] = t;
+    }
+}
+
+// sum of partials [nb][n] in block order -> out[n]
+__global__ void k_sum_rows(const float *__restrict__ part, int nb, int n, float *__restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)b * n + i];
+        out[i] = s;
+    }
+}
+
+// wgrad partials [27][nb][cout*cin] -> [27][cout*cin]
+__global__ void k_sum_wgrad(const float *__restrict__ part, int nb, int m, float *__restrict__ out) {
+    const int n = 27 * m;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int tap = i / m, e = i % m;
+        float s = 0.0f;
+        for (int b = 0; b < nb; ++b) s += part[((size_t)tap * nb + b) * m + e];
+        out[i] = s;
+    }
+}
+
+__global__ void k_adam(int n, float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2,
+                       const int *__restrict__ live) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (live && !live[i]) continue;  // padding entries stay zero
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers (dispatch over the fixed layer shapes)
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+static int conv_fwd_t(const ConvArgs &a, cudaStream_t s) {
+    MGCT_KERNEL(KK_CONV, s, k_conv_fwd<CIN, COUT, RELU, OUT_F32><<<(a.nvox + CV_M - 1) / CV_M, 128, 0, s>>>(a));
+    return MGCT_OK;
+}
+
+static int conv_forward(int l, const ConvArgs &a, cudaStream_t s) {
+    switch (l) {
+        case 0: return conv_fwd_t<16, 16, true, false>(a, s);
+        case 1: return conv_fwd_t<16, 32, true, false>(a, s);
+        case 2: return conv_fwd_t<32, 64, true, false>(a, s);
+        default: return conv_fwd_t<64, 16, false, true>(a, s);
+    }
+}
+
+// backward data of layer l: forward shape (CIN' = COUT_l, COUT' = CIN_l)
+static int conv_bwd_data(int l, const ConvArgs &a, cudaStream_t s) {
+    switch (l) {
+        case 1: return conv_fwd_t<32, 16, false, false>(a, s);
+        case 2: return conv_fwd_t<64, 32, false, false>(a, s);
+        case 3: return conv_fwd_t<16, 64, false, false>(a, s);
+        default: return set_error(MGCT_EINVAL, "no data gradient for the input layer");
+    }
+}
+
+constexpr int WG_BLOCKS = 96;  // voxel-tile groups per tap in the weight gradient
+
+template <int CIN, int COUT>
+static int conv_wgrad_t(const __nv_bfloat16 *in, const __nv_bfloat16 *gout, float *part, int B, int D, int H, int W,
+                        int nvox, cudaStream_t s) {
+    dim3 grid(WG_BLOCKS, 27);
+    MGCT_KERNEL(KK_CONV, s, k_conv_wgrad<CIN, COUT><<<grid, 128, 0, s>>>(in, gout, part, B, D, H, W, nvox));
+    return MGCT_OK;
+}
+
+static int conv_wgrad(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *gout, float *part, int B, int D, int H,
+                      int W, int nvox, cudaStream_t s) {
+    switch (l) {
+        case 0: return conv_wgrad_t<16, 16>(in, gout, part, B, D, H, W, nvox, s);
+        case 1: return conv_wgrad_t<16, 32>(in, gout, part, B, D, H, W, nvox, s);
+        case 2: return conv_wgrad_t<32, 64>(in, gout, part, B, D, H, W, nvox, s);
+        default: return conv_wgrad_t<64, 16>(in, gout, part, B, D, H, W, nvox, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+struct NetSpace {
+    __nv_bfloat16 *x0, *act[NL];  // act[l] = output of layer l (l < 3), bf16
+    float *xs, *y;                // scaled input, network output (float32)
+    __nv_bfloat16 *g[NL];         // gradient wrt the input of layer l+1 ... (g[l]: [nvox][LCOUT[l]])
+    float *wpart, *bpart;
+    double *lpart, *sumsq;
+};
+
+static size_t carve_net(int64_t nvox, bool training, char *base, NetSpace *sp) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        off = (off + 255) & ~(size_t)255;
+        char *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    NetSpace s;
+    std::memset(&s, 0, sizeof(s));
+    s.x0 = reinterpret_cast<__nv_bfloat16 *>(take((size_t)nvox * 16 * 2));
+    for (int l = 0; l < NL - 1; ++l) s.act[l] = reinterpret_cast<__nv_bfloat16 *>(take((size_t)nvox * LCOUT[l] * 2));
+    s.xs = reinterpret_cast<float *>(take((size_t)nvox * 4));
+    s.y = reinterpret_cast<float *>(take((size_t)nvox * 4));
+    s.sumsq = reinterpret_cast<double *>(take(64));
+    s.lpart = reinterpret_cast<double *>(take(1024 * 8));
+    if (training) {
+        for (int l = 0; l < NL; ++l) s.g[l] = reinterpret_cast<__nv_bfloat16 *>(take((size_t)nvox * LCOUT[l] * 2));
+        size_t mw = 0;
+        for (int l = 0; l < NL; ++l) mw = std::max(mw, wcount(l));
+        s.wpart = reinterpret_cast<float *>(take((size_t)WG_BLOCKS * mw * 4));
+        s.bpart = reinterpret_cast<float *>(take((size_t)1024 * 64 * 4));
+    }
+    if (sp) *sp = s;
+    return off + 256;
+}
+
+static int net_sumsq(const float *x, int nvox, double *out, double *lpart, cudaStream_t s);
+
+}  // namespace mgct
+
+using namespace mgct;
+
+extern "C" {
+
+size_t mgct_net_param_count(void) {
+    size_t n = 0;
+    for (int l = 0; l < NL; ++l) n += (size_t)27 * LCOUT_REAL[l] * LCIN_REAL[l] + LCOUT_REAL[l];
+    return n;
+}
+
+size_t mgct_net_workspace_bytes(int64_t nvox, int training) {
+    if (nvox <= 0) return 0;
+    return carve_net(nvox, training != 0, nullptr, nullptr);
+}
+
+void mgct_net_destroy(mgct_net *net) {
+    if (!net) return;
+    for (int l = 0; l < NL; ++l) {
+        void *ps[] = {net->w[l], net->b[l], net->mw[l], net->vw[l], net->mb[l], net->vb[l], net->gw[l], net->gb[l],
+                      net->wf[l], net->wt[l]};
+        for (void *p : ps)
+            if (p) cudaFree(p);
+    }
+    if (net->loss) cudaFree(net->loss);
+    delete net;
+}
+
+// Parameters are exchanged as float32, layer by layer: the real weights
+// [27][cout_real][cin_real] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)) then the
+// real biases [cout_real].
+int mgct_net_set_params(mgct_net *net, const float *host, size_t count) {
+    if (!net || !host) return set_error(MGCT_EINVAL, "net and params must not be NULL");
+    if (count != mgct_net_param_count()) return set_error(MGCT_ESHAPE, "wrong parameter count");
+    size_t off = 0;
+    for (int l = 0; l < NL; ++l) {
+        std::vector<float> w(wcount(l), 0.0f), b(LCOUT[l], 0.0f);
+        for (int tap = 0; tap < 27; ++tap)
+            for (int co = 0; co < LCOUT_REAL[l]; ++co)
+                for (int ci = 0; ci < LCIN_REAL[l]; ++ci)
+                    w[((size_t)tap * LCOUT[l] + co) * LCIN[l] + ci] = host[off++];
+        for (int co = 0; co < LCOUT_REAL[l]; ++co) b[co] = host[off++];
+        MGCT_TRY(check_cuda(cudaMemcpy(net->w[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice), "set params"));
+        MGCT_TRY(check_cuda(cudaMemcpy(net->b[l], b.data(), b.size() * 4, cudaMemcpyHostToDevice), "set params"));
+        k_pack_weights<<<64, 256>>>(net->w[l], net->wf[l], net->wt[l], LCOUT[l], LCIN[l]);
+        count_launch();
+        MGCT_LAUNCH_CHECK("pack weights");
+    }
+    return check_cuda(cudaDeviceSynchronize(), "set params");
+}
+
+static int get_tensors(const mgct_net *net, float *const *src_w, float *const *src_b, float *host) {
+    size_t off = 0;
+    for (int l = 0; l < NL; ++l) {
+        std::vector<float> w(wcount(l)), b(LCOUT[l]);
+        MGCT_TRY(check_cuda(cudaMemcpy(w.data(), src_w[l], w.size() * 4, cudaMemcpyDeviceToHost), "get params"));
+        MGCT_TRY(check_cuda(cudaMemcpy(b.data(), src_b[l], b.size() * 4, cudaMemcpyDeviceToHost), "get params"));
+        for (int tap = 0; tap < 27; ++tap)
+            for (int co = 0; co < LCOUT_REAL[l]; ++co)
+                for (int ci = 0; ci < LCIN_REAL[l]; ++ci) host[off++] = w[((size_t)tap * LCOUT[l] + co) * LCIN[l] + ci];
+        for (int co = 0; co < LCOUT_REAL[l]; ++co) host[off++] = b[co];
+    }
+    return MGCT_OK;
+}
+
+int mgct_net_get_params(const mgct_net *net, float *host, size_t count) {
+    if (!net || !host) return set_error(MGCT_EINVAL, "net and params must not be NULL");
+    if (count != mgct_net_param_count()) return set_error(MGCT_ESHAPE, "wrong parameter count");
+    return get_tensors(net, net->w, net->b, host);
+}
+
+int mgct_net_get_grads(const mgct_net *net, float *host, size_t count) {
+    if (!net || !host) return set_error(MGCT_EINVAL, "net and grads must not be NULL");
+    if (count != mgct_net_param_count()) return set_error(MGCT_ESHAPE, "wrong parameter count");
+    MGCT_TRY(check_cuda(cudaDeviceSynchronize(), "get grads"));
+    return get_tensors(net, net->gw, net->gb, host);
+}
+
+int mgct_net_create(uint64_t seed, mgct_net **out) {
+    if (!out) return set_error(MGCT_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    mgct_net *net = new mgct_net();
+    std::memset(net, 0, sizeof(*net));
+    int st = MGCT_OK;
+    for (int l = 0; l < NL && !st; ++l) {
+        const size_t nw = wcount(l) * 4, nb = (size_t)LCOUT[l] * 4;
+        float **fl[] = {&net->w[l], &net->mw[l], &net->vw[l], &net->gw[l]};
+        for (float **p : fl)
+            if (!st) st = check_cuda(cudaMalloc(p, nw), "net alloc");
+        float **fb[] = {&net->b[l], &net->mb[l], &net->vb[l], &net->gb[l]};
+        for (float **p : fb)
+            if (!st) st = check_cuda(cudaMalloc(p, nb), "net alloc");
+        if (!st) st = check_cuda(cudaMalloc(&net->wf[l], wcount(l) * 2), "net alloc");
+        if (!st) st = check_cuda(cudaMalloc(&net->wt[l], wcount(l) * 2), "net alloc");
+        if (!st) {
+            cudaMemset(net->mw[l], 0, nw);
+            cudaMemset(net->vw[l], 0, nw);
+            cudaMemset(net->gw[l], 0, nw);
+            cudaMemset(net->mb[l], 0, nb);
+            cudaMemset(net->vb[l], 0, nb);
+            cudaMemset(net->gb[l], 0, nb);
+        }
+    }
+    if (!st) st = check_cuda(cudaMalloc(&net->loss, 8), "net alloc");
+    if (st) {
+        mgct_net_destroy(net);
+        return st;
+    }
+    // He-normal initialisation (fan-in 27 cin_real), zero biases; the output
+    // layer starts at zero so that the initial correction is none.
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<float> params(mgct_net_param_count());
+    size_t off = 0;
+    for (int l = 0; l < NL; ++l) {
+        const double sd = l == NL - 1 ? 0.0 : std::sqrt(2.0 / (27.0 * LCIN_REAL[l]));
+        for (size_t i = 0; i < (size_t)27 * LCOUT_REAL[l] * LCIN_REAL[l]; ++i) params[off++] = (float)(sd * nd(rng));
+        for (int co = 0; co < LCOUT_REAL[l]; ++co) params[off++] = 0.0f;
+    }
+    st = mgct_net_set_params(net, params.data(), params.size());
+    if (st) {
+        mgct_net_destroy(net);
+        return st;
+    }
+    net->step = 0;
+    *out = net;
+    return MGCT_OK;
+}
+
+// forward pass on [B][D][H][W] voxels; x float32 [nvox]; scale: when
+// `normalise`, x is divided by its RMS (computed here).  Leaves the
+// activations in the workspace.
+static int net_forward(const mgct_net *net, int B, int D, int H, int W, const float *x, bool normalise,
+                       const NetSpace &sp, cudaStream_t s) {
+    const int nvox = B * D * H * W;
+    const double *ss = nullptr;
+    if (normalise) {
+        MGCT_TRY(net_sumsq(x, nvox, sp.sumsq, sp.lpart, s));
+        ss = sp.sumsq;
+    }
+    MGCT_KERNEL(KK_CONV, s, k_net_input<<<std::min((nvox + 255) / 256, 152 * 32), 256, 0, s>>>(x, ss, nvox, sp.x0, sp.xs));
+    const __nv_bfloat16 *cur = sp.x0;
+    for (int l = 0; l < NL; ++l) {
+        ConvArgs a;
+        a.in = cur;
+        a.w = net->wf[l];
+        a.bias = net->b[l];
+        a.mask = nullptr;
+        a.B = B;
+        a.D = D;
+        a.H = H;
+        a.W = W;
+        a.nvox = nvox;
+        if (l < NL - 1) {
+            a.out = sp.act[l];
+            a.out_ch = LCOUT[l];
+            a.out_stride = LCOUT[l];
+        } else {
+            a.out = sp.y;
+            a.out_ch = 1;
+            a.out_stride = 1;
+        }
+        MGCT_TRY(conv_forward(l, a, s));
+        if (l < NL - 1) cur = sp.act[l];
+    }
+    return MGCT_OK;
+}
+
+}  // extern "C"
+
+namespace mgct {
+
+__global__ void k_sumsq_f(const float *__restrict__ x, int n, double *__restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) s += (double)x[p] * x[p];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+static int net_sumsq(const float *x, int nvox, double *out, double *lpart, cudaStream_t s) {
+    const int nb = std::min(1024, (nvox + 255) / 256);
+    MGCT_KERNEL(KK_REDUCE, s, k_sumsq_f<<<nb, 256, 0, s>>>(x, nvox, lpart));
+    return launch_sum_partials(lpart, nb, 1, out, s);
+}
+
+}  // namespace mgct
+
+extern "C" {
+
+int mgct_net_apply(const mgct_net *net, int B, int D, int H, int W, const float *dir, float *out, void *ws,
+                   size_t ws_bytes, mgct_stream stream) {
+    if (!net) return set_error(MGCT_EINVAL, "net is NULL");
+    MGCT_TRY(check_ptr(dir, "dir"));
+    MGCT_TRY(check_ptr(out, "out"));
+    MGCT_TRY(check_ptr(ws, "workspace"));
+    if (B < 1 || D < 1 || H < 1 || W < 1 || (int64_t)B * D * H * W > ((int64_t)1 << 31) - 1)
+        return set_error(MGCT_ESHAPE, "bad volume dimensions");
+    const int64_t nvox = (int64_t)B * D * H * W;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < mgct_net_workspace_bytes(nvox, 0))
+        return set_error(MGCT_ENOMEM, "net workspace too small or misaligned");
+    NetSpace sp;
+    carve_net(nvox, false, static_cast<char *>(ws), &sp);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MGCT_TRY(net_forward(net, B, D, H, W, dir, true, sp, s));
+    MGCT_KERNEL(KK_CONV, s, k_net_output<<<std::min((int)((nvox + 255) / 256), 152 * 32), 256, 0, s>>>(sp.xs, sp.y, sp.sumsq, (int)nvox, out));
+    return MGCT_OK;
+}
+
+int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const float *x, const float *t, void *ws,
+                              size_t ws_bytes, double *loss, mgct_stream stream) {
+    if (!net) return set_error(MGCT_EINVAL, "net is NULL");
+    MGCT_TRY(check_ptr(x, "x"));
+    MGCT_TRY(check_ptr(t, "t"));
+    MGCT_TRY(check_ptr(ws, "workspace"));
+    if (B < 1 || D < 1 || H < 1 || W < 1 || (int64_t)B * D * H * W > ((int64_t)1 << 31) - 1)
+        return set_error(MGCT_ESHAPE, "bad volume dimensions");
+    const int nvox = B * D * H * W;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < mgct_net_workspace_bytes(nvox, 1))
+        return set_error(MGCT_ENOMEM, "net workspace too small or misaligned");
+    NetSpace sp;
+    carve_net(nvox, true, static_cast<char *>(ws), &sp);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // x and t are already in scaled units
+    MGCT_TRY(net_forward(net, B, D, H, W, x, false, sp, s));
+    const int nb = std::min(1024, (nvox + 255) / 256);
+    MGCT_KERNEL(KK_CONV, s, k_mse<<<nb, 256, 0, s>>>(sp.xs, sp.y, t, nvox, sp.g[NL - 1], sp.lpart));
+    MGCT_TRY(launch_sum_partials(sp.lpart, nb, 1, net->loss, s));
+    // backward through the layers; g[l] = dL/d(output of layer l)
+    for (int l = NL - 1; l >= 0; --l) {
+        const __nv_bfloat16 *lin = l == 0 ? sp.x0 : sp.act[l - 1];
+        MGCT_TRY(conv_wgrad(l, lin, sp.g[l], sp.wpart, B, D, H, W, nvox, s));
+        const int m = LCOUT[l] * LCIN[l];
+        MGCT_KERNEL(KK_CONV, s, k_sum_wgrad<<<(27 * m + 255) / 256, 256, 0, s>>>(sp.wpart, WG_BLOCKS, m, net->gw[l]));
+        const int cb = std::min(1024, (nvox + 255) / 256);
+        MGCT_KERNEL(KK_CONV, s, k_channel_sums<<<cb, 256, 0, s>>>(sp.g[l], nvox, LCOUT[l], sp.bpart));
+        MGCT_KERNEL(KK_CONV, s, k_sum_rows<<<1, 64, 0, s>>>(sp.bpart, cb, LCOUT[l], net->gb[l]));
+        if (l > 0) {
+            ConvArgs a;
+            a.in = sp.g[l];
+            a.w = net->wt[l];
+            a.bias = nullptr;
+            a.mask = sp.act[l - 1];  // ReLU of the previous layer
+            a.out = sp.g[l - 1];
+            a.B = B;
+            a.D = D;
+            a.H = H;
+            a.W = W;
+            a.nvox = nvox;
+            a.out_ch = LCIN[l];
+            a.out_stride = LCIN[l];
+            MGCT_TRY(conv_bwd_data(l, a, s));
+        }
+    }
+    if (loss) MGCT_TRY(check_cuda(cudaMemcpyAsync(loss, net->loss, 8, cudaMemcpyDeviceToDevice, s), "loss copy"));
+    return MGCT_OK;
+}
+
+int mgct_net_adam_step(mgct_net *net, double lr, mgct_stream stream) {
+    if (!net) return set_error(MGCT_EINVAL, "net is NULL");
+    if (!(lr >= 0.0)) return set_error(MGCT_EINVAL, "lr must be >= 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    net->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)net->step));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)net->step));
+    for (int l = 0; l < NL; ++l) {
+        const int nw = (int)wcount(l);
+        MGCT_KERNEL(KK_UPDATE, s, k_adam<<<(nw + 255) / 256, 256, 0, s>>>(nw, net->w[l], net->gw[l], net->mw[l], net->vw[l], (float)lr, b1, b2, eps, c1, c2, nullptr));
+        MGCT_KERNEL(KK_UPDATE, s, k_adam<<<1, 64, 0, s>>>(LCOUT[l], net->b[l], net->gb[l], net->mb[l], net->vb[l], (float)lr, b1, b2, eps, c1, c2, nullptr));
+        MGCT_KERNEL(KK_UPDATE, s, k_pack_weights<<<64, 256, 0, s>>>(net->w[l], net->wf[l], net->wt[l], LCOUT[l], LCIN[l]));
+    }
+    return MGCT_OK;
+}
+
+}  // extern "C"

@@ -359,3 +359,100 @@ def project_residual_static(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, 
                                               _ptr(out, "out", torch.float32), _ptr(b, "b", torch.float32),
                                               _ptr(sumsq, "sumsq", torch.float64), _stream()))
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned preconditioner correction (mgct_net_*)
+# ---------------------------------------------------------------------------
+_net_sigs_done = False
+
+
+def _net_sigs():
+    global _net_sigs_done
+    if _net_sigs_done:
+        return lib()
+    L = lib()
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    L.mgct_net_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.mgct_net_destroy.argtypes = [vp]
+    L.mgct_net_destroy.restype = None
+    L.mgct_net_param_count.restype = sz
+    L.mgct_net_set_params.argtypes = [vp, vp, sz]
+    L.mgct_net_get_params.argtypes = [vp, vp, sz]
+    L.mgct_net_get_grads.argtypes = [vp, vp, sz]
+    L.mgct_net_workspace_bytes.argtypes = [ctypes.c_int64, i]
+    L.mgct_net_workspace_bytes.restype = sz
+    L.mgct_net_apply.argtypes = [vp, i, i, i, i, vp, vp, vp, sz, vp]
+    L.mgct_net_forward_backward.argtypes = [vp, i, i, i, i, vp, vp, vp, sz, vp, vp]
+    L.mgct_net_adam_step.argtypes = [vp, ctypes.c_double, vp]
+    for fn in ("mgct_net_create", "mgct_net_set_params", "mgct_net_get_params", "mgct_net_get_grads",
+               "mgct_net_apply", "mgct_net_forward_backward", "mgct_net_adam_step"):
+        getattr(L, fn).restype = ctypes.c_int
+    _net_sigs_done = True
+    return L
+
+
+class Net:
+    """The learned correction network (mgct_net_create)."""
+
+    def __init__(self, seed: int = 0):
+        L = _net_sigs()
+        h = ctypes.c_void_p()
+        _check(L.mgct_net_create(ctypes.c_uint64(seed), ctypes.byref(h)))
+        self.handle = h
+        self.count = int(L.mgct_net_param_count())
+        self._ws = None
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.count, dtype=np.float32)
+        _check(_net_sigs().mgct_net_get_params(self.handle, out.ctypes.data, self.count))
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(_net_sigs().mgct_net_set_params(self.handle, p.ctypes.data, p.size))
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.count, dtype=np.float32)
+        _check(_net_sigs().mgct_net_get_grads(self.handle, out.ctypes.data, self.count))
+        return out
+
+    def _workspace(self, nvox: int, training: bool) -> torch.Tensor:
+        need = int(_net_sigs().mgct_net_workspace_bytes(nvox, 1 if training else 0))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def apply(self, step: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Corrected step s (x + f(x)), x = step / RMS(step); step [B][D][H][W] or [D][H][W]."""
+        shp = step.shape if step.dim() == 4 else (1,) + tuple(step.shape)
+        if out is None:
+            out = torch.empty_like(step)
+        ws = self._workspace(int(np.prod(shp)), False)
+        _check(_net_sigs().mgct_net_apply(self.handle, *shp, _ptr(step, "step", torch.float32),
+                                          _ptr(out, "out", torch.float32), _ptr(ws, "ws"), ws.numel(), _stream()))
+        return out
+
+    def forward_backward(self, x: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+        """Loss mean((x + f(x) - t)^2) (device float64) and parameter gradients."""
+        shp = x.shape if x.dim() == 4 else (1,) + tuple(x.shape)
+        ws = self._workspace(int(np.prod(shp)), True)
+        _check(_net_sigs().mgct_net_forward_backward(self.handle, *shp, _ptr(x, "x", torch.float32),
+                                                     _ptr(t, "t", torch.float32), _ptr(ws, "ws"), ws.numel(),
+                                                     _ptr(self.loss, "loss", torch.float64), _stream()))
+        return self.loss
+
+    def adam_step(self, lr: float) -> None:
+        _check(_net_sigs().mgct_net_adam_step(self.handle, float(lr), _stream()))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _net_sigs().mgct_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

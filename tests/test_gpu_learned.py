@@ -1,0 +1,120 @@
+"""Learned correction network on the GPU (BF16 tensor-core convolutions,
+float32 accumulation) against the FP64 oracle of the same network.
+
+Tolerance, from the arithmetic: the GPU stores the input, the weights, the
+hidden activations and the back-propagated gradients in bfloat16 (unit
+roundoff u = 2^-9) and accumulates in float32.  The oracle with bf16=True
+rounds the same tensors at the same places, so what remains is the float32
+accumulation order and the occasional different rounding of a value that
+falls near a bf16 rounding boundary: errors of a few u relative to the
+largest entry.  The bound used is 8u = 1.6 %."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import learned as NL
+from tests.helpers import to_np
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2103_10329_gb300 import build
+    build.build()
+
+
+def random_params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    layers = []
+    for ci, co in zip(NL.CIN, NL.COUT):
+        sd = scale * np.sqrt(2.0 / (27 * ci))
+        layers.append((rng.standard_normal((27, co, ci)) * sd, rng.standard_normal(co) * 0.1))
+    return NL.pack(layers).astype(np.float32)
+
+
+def test_param_layout_roundtrip():
+    from paper_2103_10329_gb300 import mgct
+    net = mgct.Net(seed=3)
+    assert net.count == NL.param_count()
+    p = random_params(1)
+    net.set_params(p)
+    np.testing.assert_array_equal(net.params(), p)
+    # the default initialisation has a zero output layer: no correction
+    net0 = mgct.Net(seed=4)
+    step = torch.randn((1, 8, 9, 10), device="cuda")
+    out = net0.apply(step)
+    torch.cuda.synchronize()
+    assert torch.allclose(out, step, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("shape", [(1, 16, 16, 16), (2, 7, 12, 19)])
+def test_forward_vs_oracle(shape):
+    from paper_2103_10329_gb300 import mgct
+    net = mgct.Net()
+    p = random_params(5)
+    net.set_params(p)
+    step = 0.01 * np.random.default_rng(6).standard_normal(shape)
+    out = to_np(net.apply(torch.tensor(step, dtype=torch.float32, device="cuda")))
+    s = np.sqrt(np.mean(step.astype(np.float32).astype(np.float64) ** 2))
+    x = step.astype(np.float32).astype(np.float64) / s
+    y_bf, _ = NL.forward(p.astype(np.float64), x, bf=True)
+    y_64, _ = NL.forward(p.astype(np.float64), x, bf=False)
+    y_gpu = out / s - x
+    scale = np.abs(y_64).max()
+    assert np.abs(y_gpu - y_bf).max() <= 8 * U * scale
+    assert np.abs(y_gpu - y_64).max() <= 32 * U * scale
+
+
+def test_gradients_vs_oracle():
+    from paper_2103_10329_gb300 import mgct
+    net = mgct.Net()
+    p = random_params(7)
+    net.set_params(p)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((2, 10, 12, 14))
+    t = x + 0.5 * rng.standard_normal(x.shape)
+    xf, tf = x.astype(np.float32), t.astype(np.float32)
+    loss = net.forward_backward(torch.tensor(xf, device="cuda"), torch.tensor(tf, device="cuda"))
+    g_gpu = net.grads().astype(np.float64)
+    l_ref, g_ref = NL.loss_and_grads(p.astype(np.float64), xf.astype(np.float64), tf.astype(np.float64), bf=True)
+    assert abs(loss.item() - l_ref) <= 8 * U * l_ref
+    layers_gpu = NL.unpack(g_gpu)
+    layers_ref = NL.unpack(g_ref)
+    for l, ((wg, bg), (wr, br)) in enumerate(zip(layers_gpu, layers_ref)):
+        assert np.linalg.norm(wg - wr) <= 8 * U * np.linalg.norm(wr), (l, np.linalg.norm(wg - wr) / np.linalg.norm(wr))
+        assert np.linalg.norm(bg - br) <= 8 * U * np.linalg.norm(br) + 1e-12, l
+
+
+def test_adam_step():
+    from paper_2103_10329_gb300 import mgct
+    net = mgct.Net()
+    p = random_params(9)
+    net.set_params(p)
+    rng = np.random.default_rng(10)
+    x = torch.tensor(rng.standard_normal((1, 8, 8, 8)), dtype=torch.float32, device="cuda")
+    t = x + 0.3
+    net.forward_backward(x, t)
+    g = net.grads().astype(np.float64)
+    net.adam_step(1e-3)
+    q = net.params().astype(np.float64)
+    # first Adam step: m = 0.1 g, v = 0.001 g^2, bias corrections 0.1 and 0.001
+    want = p.astype(np.float64) - 1e-3 * g / (np.abs(g) + 1e-8)
+    np.testing.assert_allclose(q, want, rtol=1e-5, atol=1e-7)
+
+
+def test_deterministic_training_step():
+    from paper_2103_10329_gb300 import mgct
+    rng = np.random.default_rng(11)
+    x = torch.tensor(rng.standard_normal((2, 9, 9, 9)), dtype=torch.float32, device="cuda")
+    t = 0.5 * x
+    outs = []
+    for _ in range(2):
+        net = mgct.Net(seed=12)
+        net.set_params(random_params(13))
+        for _ in range(3):
+            net.forward_backward(x, t)
+            net.adam_step(1e-3)
+        outs.append(net.params())
+    np.testing.assert_array_equal(outs[0], outs[1])

@@ -231,6 +231,23 @@ int mgct_multigrid_iteration(const mgct_geom *geom, float *vol, const float *b, 
                              size_t ws_bytes, const mgct_lw_opts *opts, mgct_lw_stats *stats,
                              mgct_stream stream);
 
+/* Alg. 1 without the grid-0 Landweber step: restrict mu, recurse (or one
+ * OS-EMTR pass on the coarsest grid) and add the prolongated coarse change.
+ * mgct_multigrid_iteration = mgct_multigrid_coarse + mgct_landweber_step at
+ * grid 0.  Same arguments as mgct_multigrid_iteration without b. */
+int mgct_multigrid_coarse(const mgct_geom *geom, float *vol, void *workspace, size_t ws_bytes,
+                          const mgct_lw_opts *opts, mgct_lw_stats *stats, mgct_stream stream);
+
+/* The step alpha d of one Landweber step (Eq. 4: d = p * A^T (b - A mu),
+ * alpha from the line search or fixed) into step (float32 [n_g]^3), without
+ * changing vol.  Used to collect training pairs for the learned correction. */
+int mgct_landweber_direction(const mgct_geom *geom, int level, const float *vol, const float *b,
+                             void *workspace, size_t ws_bytes, const mgct_lw_opts *opts,
+                             float *step, mgct_lw_stats *stats, mgct_stream stream);
+
+/* y += a x, float32 (count elements). */
+int mgct_axpy(size_t count, float a, const float *x, float *y, mgct_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Geometry gradient (Sec. 1: drift of the source and detector, estimated
  * jointly with the image).  dphi[i][5] = d/dphi of sum_rays y * (A vol) over
@@ -282,6 +299,19 @@ int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const f
                               const float *t, void *workspace, size_t ws_bytes, double *loss,
                               mgct_stream stream);
 int mgct_net_adam_step(mgct_net *net, double lr, mgct_stream stream);
+
+/* Learned Landweber step on grid `level`: the plain step alpha d (Eq. 4 with
+ * the exact line search), the corrected step d' = mgct_net_apply(alpha d),
+ * a second exact line search beta = <r, A d'> / |A d'|^2, and the update
+ * mu <- S_lambda(mu + beta d'), or mu <- S_lambda(mu + alpha d) when beta is
+ * not positive and finite (the plain filter is the fallback).  opts->alpha
+ * must be <= 0.  net_ws: mgct_net_workspace_bytes(n_g^3, 0) bytes.  stats:
+ * device double[8] = {alpha, r2, r2_pred, nonfinite, beta, r2, r2_pred
+ * (learned), nonfinite}. */
+int mgct_landweber_learned(const mgct_geom *geom, int level, float *vol, const float *b,
+                           void *workspace, size_t ws_bytes, const mgct_lw_opts *opts,
+                           const mgct_net *net, void *net_ws, size_t net_ws_bytes, double *stats,
+                           mgct_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Residual projection without any device allocation.  The paper has no

@@ -22,6 +22,10 @@ int launch_update(size_t count, float *mu, const float *d, const double *alpha, 
 int launch_em_update(size_t count, float *mu, const float *nd, double *part, cudaStream_t s);
 int launch_fill(size_t count, float *x, float v, cudaStream_t s);
 int launch_copy(size_t count, const float *in, float *out, cudaStream_t s);
+int launch_scaled_copy(size_t count, const float *d, const double *alpha, float *out, cudaStream_t s);
+int launch_update_choice(size_t count, float *mu, const float *d, const float *dl, const double *st, float lam,
+                         cudaStream_t s);
+int launch_axpy(size_t count, float a, const float *x, float *y, cudaStream_t s);
 
 int launch_column_table(const mgct_geom *g, int level, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
@@ -142,18 +146,17 @@ static int check_ws(const mgct_geom *g, int op, int level, const void *ws, size_
 // ---------------------------------------------------------------------------
 // ST: storage type of the copies the projector and back-projector read (the
 // shadow of mu, the residual sinogram, the shadow of the search direction).
+//
+// Phase 1 (direction): r = b - A mu (stored weighted, |r|^2 into sums[0]),
+// grad = A^T r, d = p * grad (or grad).  Returns d.
 template <typename ST>
-static int landweber_t(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
-                       mgct_lw_stats *stats_out, cudaStream_t s) {
+static int lw_direction(const mgct_geom *g, int level, const float *mu, const float *b, const LWSpace &w,
+                        const mgct_lw_opts &o, float **d_out, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
-    Carver c(ws);
-    LWSpace w = carve_lw(g, level, c);
     const int K = g->desc.n_views;
     const size_t nv3 = vox(L);
-    double *stats = stats_out ? reinterpret_cast<double *>(stats_out) : w.stats;
     constexpr bool F32 = std::is_same<ST, float>::value;
     MGCT_TRY(check_cuda(cudaMemsetAsync(w.sums, 0, 8 * sizeof(double), s), "memset"));
-    // projector inputs: mu itself (+ x-major copy), or 16-bit shadows of both
     const ST *muS;
     const ST *muST;
     if constexpr (F32) {
@@ -166,41 +169,100 @@ static int landweber_t(const mgct_geom *g, int level, float *mu, const float *b,
         muS = a;
         muST = a + nv3;
     }
-    // r = b - A mu, stored weighted by each ray's dl; |r|^2 in float64
     ST *r = reinterpret_cast<ST *>(w.r);
     int nb = 0;
     EpiResidual<ST, true> er{r, b, w.part, L.nu, L.nv, K};
     MGCT_TRY(launch_project<ST>(g, level, 0, K, 1, muS, muST, er, s, &nb));
     MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
-    // d = p * A^T r   (or A^T r for SIRT), float32
     MGCT_TRY(launch_backproject<1, ST, true>(g, level, 0, K, 1, r, w.grad, 0, s));
-    float *d = w.grad, *spare = w.d;
+    *d_out = w.grad;
     if (o.precondition) {
         MGCT_TRY(launch_precondition(L.n, g->desc.p_slice_axis, w.grad, w.d, s));
-        d = w.d;
-        spare = w.grad;  // the gradient is no longer needed
+        *d_out = w.d;
     }
-    if (!(o.alpha > 0.0)) {
-        // exact line search along d: <r, A d>, |A d|^2
-        const ST *dS;
-        const ST *dST;
-        if constexpr (F32) {
-            MGCT_TRY(launch_transpose_xy<float>(L.n, d, spare, s));
-            dS = d;
-            dST = spare;
-        } else {
-            ST *a = reinterpret_cast<ST *>(spare);
-            MGCT_TRY(launch_cast_transpose<ST>(L.n, d, a, a + nv3, s));
-            dS = a;
-            dST = a + nv3;
-        }
-        EpiDualDot<ST> ed{r, w.part, L.nu, L.nv, K};
-        MGCT_TRY(launch_project<ST>(g, level, 0, K, 1, dS, dST, ed, s, &nb));
-        MGCT_TRY(launch_sum_partials(w.part, nb, 2, w.sums + 1, s));
-    }
-    MGCT_TRY(launch_step_size(w.sums + 1, w.sums + 0, o.alpha > 0.0 ? o.alpha : 0.0, stats, s));
-    MGCT_TRY(launch_update(nv3, mu, d, stats, (float)o.lambda, s));
     return MGCT_OK;
+}
+
+// Phase 2 (line search along dir): <r, A dir>, |A dir|^2 into sums[slot],
+// sums[slot+1]; `spare` (one float32 volume) holds the projector's copies.
+template <typename ST>
+static int lw_line_search(const mgct_geom *g, int level, const float *dir, float *spare, const LWSpace &w, int slot,
+                          cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    const int K = g->desc.n_views;
+    const size_t nv3 = vox(L);
+    const ST *dS;
+    const ST *dST;
+    if constexpr (std::is_same<ST, float>::value) {
+        MGCT_TRY(launch_transpose_xy<float>(L.n, dir, spare, s));
+        dS = dir;
+        dST = spare;
+    } else {
+        ST *a = reinterpret_cast<ST *>(spare);
+        MGCT_TRY(launch_cast_transpose<ST>(L.n, dir, a, a + nv3, s));
+        dS = a;
+        dST = a + nv3;
+    }
+    int nb = 0;
+    EpiDualDot<ST> ed{reinterpret_cast<ST *>(w.r), w.part, L.nu, L.nv, K};
+    MGCT_TRY(launch_project<ST>(g, level, 0, K, 1, dS, dST, ed, s, &nb));
+    return launch_sum_partials(w.part, nb, 2, w.sums + slot, s);
+}
+
+template <typename ST>
+static int landweber_t(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
+                       mgct_lw_stats *stats_out, cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    Carver c(ws);
+    LWSpace w = carve_lw(g, level, c);
+    double *stats = stats_out ? reinterpret_cast<double *>(stats_out) : w.stats;
+    float *d = nullptr;
+    MGCT_TRY(lw_direction<ST>(g, level, mu, b, w, o, &d, s));
+    float *spare = d == w.d ? w.grad : w.d;  // the gradient is no longer needed
+    if (!(o.alpha > 0.0)) MGCT_TRY(lw_line_search<ST>(g, level, d, spare, w, 1, s));
+    MGCT_TRY(launch_step_size(w.sums + 1, w.sums + 0, o.alpha > 0.0 ? o.alpha : 0.0, stats, s));
+    return launch_update(vox(L), mu, d, stats, (float)o.lambda, s);
+}
+
+// The step alpha d of one Landweber step (no update), into out.
+template <typename ST>
+static int direction_t(const mgct_geom *g, int level, const float *mu, const float *b, void *ws, const mgct_lw_opts &o,
+                       float *out, mgct_lw_stats *stats_out, cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    Carver c(ws);
+    LWSpace w = carve_lw(g, level, c);
+    double *stats = stats_out ? reinterpret_cast<double *>(stats_out) : w.stats;
+    float *d = nullptr;
+    MGCT_TRY(lw_direction<ST>(g, level, mu, b, w, o, &d, s));
+    float *spare = d == w.d ? w.grad : w.d;
+    if (!(o.alpha > 0.0)) MGCT_TRY(lw_line_search<ST>(g, level, d, spare, w, 1, s));
+    MGCT_TRY(launch_step_size(w.sums + 1, w.sums + 0, o.alpha > 0.0 ? o.alpha : 0.0, stats, s));
+    return launch_scaled_copy(vox(L), d, stats, out, s);
+}
+
+// Learned Landweber step: step = alpha d as usual, corrected step d' =
+// net(alpha d), a second exact line search beta along d', and the update
+// mu += beta d' (or alpha d when beta <= 0).  stats: 8 doubles, the plain
+// {alpha, r2, r2_pred, nonfinite} then the learned {beta, r2, r2_pred, nonfinite}.
+template <typename ST>
+static int learned_t(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
+                     const mgct_net *net, void *net_ws, size_t net_bytes, double *stats, cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    Carver c(ws);
+    LWSpace w = carve_lw(g, level, c);
+    const size_t nv3 = vox(L);
+    float *d = nullptr;
+    MGCT_TRY(lw_direction<ST>(g, level, mu, b, w, o, &d, s));
+    float *spare = d == w.d ? w.grad : w.d;
+    MGCT_TRY(lw_line_search<ST>(g, level, d, spare, w, 1, s));
+    MGCT_TRY(launch_step_size(w.sums + 1, w.sums + 0, 0.0, stats, s));
+    float *step = spare;       // alpha d
+    float *dl = w.muT;         // net(alpha d); muT is free after the residual
+    MGCT_TRY(launch_scaled_copy(nv3, d, stats, step, s));
+    MGCT_TRY(mgct_net_apply(net, 1, L.n, L.n, L.n, step, dl, net_ws, net_bytes, reinterpret_cast<mgct_stream>(s)));
+    MGCT_TRY(lw_line_search<ST>(g, level, dl, spare, w, 3, s));
+    MGCT_TRY(launch_step_size(w.sums + 3, w.sums + 0, 0.0, stats + 4, s));
+    return launch_update_choice(nv3, mu, d, dl, stats, (float)o.lambda, s);
 }
 
 static int landweber(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
@@ -232,7 +294,7 @@ static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *
 }
 
 static int multigrid_level(const mgct_geom *g, int level, float *mu, const MGSpace &m, const float *b0,
-                           const mgct_lw_opts &o, mgct_lw_stats *stats, cudaStream_t s) {
+                           const mgct_lw_opts &o, mgct_lw_stats *stats, cudaStream_t s, bool skip_landweber = false) {
     const int Lc = g->levels;
     if (level + 1 < Lc) {
         const int nf = g->lev[level].n;
@@ -247,6 +309,7 @@ static int multigrid_level(const mgct_geom *g, int level, float *mu, const MGSpa
         }
         MGCT_TRY(launch_prolong_add(g->lev[level + 1].n, mc, oc, mu, s));
     }
+    if (skip_landweber) return MGCT_OK;
     const float *b = level == 0 ? b0 : m.b[level];
     return landweber(g, level, mu, b, m.lw_base, o, stats ? stats + level : nullptr, s);
 }
@@ -435,6 +498,60 @@ int mgct_multigrid_iteration(const mgct_geom *g, float *vol, const float *b, voi
     Carver c(ws);
     MGSpace m = carve_mg(g, c);
     return multigrid_level(g, 0, vol, m, b, *o, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgct_multigrid_coarse(const mgct_geom *g, float *vol, void *ws, size_t bytes, const mgct_lw_opts *o,
+                          mgct_lw_stats *stats, mgct_stream stream) {
+    if (!g) return set_error(MGCT_EINVAL, "geometry handle is NULL");
+    MGCT_TRY(check_opts(o));
+    MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(stats, "stats", true));
+    MGCT_TRY(check_ws(g, MGCT_WS_MULTIGRID, 0, ws, bytes));
+    Carver c(ws);
+    MGSpace m = carve_mg(g, c);
+    return multigrid_level(g, 0, vol, m, nullptr, *o, stats, reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+int mgct_landweber_direction(const mgct_geom *g, int level, const float *vol, const float *b, void *ws, size_t bytes,
+                             const mgct_lw_opts *o, float *step, mgct_lw_stats *stats, mgct_stream stream) {
+    MGCT_TRY(validate_level(g, level));
+    MGCT_TRY(check_opts(o));
+    MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(b, "b"));
+    MGCT_TRY(check_ptr(step, "step"));
+    MGCT_TRY(check_ptr(stats, "stats", true));
+    MGCT_TRY(check_ws(g, MGCT_WS_LANDWEBER, level, ws, bytes));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (o->storage) {
+        case MGCT_BF16: return direction_t<__nv_bfloat16>(g, level, vol, b, ws, *o, step, stats, s);
+        case MGCT_F16: return direction_t<__half>(g, level, vol, b, ws, *o, step, stats, s);
+        default: return direction_t<float>(g, level, vol, b, ws, *o, step, stats, s);
+    }
+}
+
+int mgct_landweber_learned(const mgct_geom *g, int level, float *vol, const float *b, void *ws, size_t bytes,
+                           const mgct_lw_opts *o, const mgct_net *net, void *net_ws, size_t net_bytes,
+                           double *stats, mgct_stream stream) {
+    MGCT_TRY(validate_level(g, level));
+    MGCT_TRY(check_opts(o));
+    if (!net) return set_error(MGCT_EINVAL, "net is NULL");
+    if (o->alpha > 0.0) return set_error(MGCT_EINVAL, "the learned step always line-searches (opts->alpha must be <= 0)");
+    MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(b, "b"));
+    MGCT_TRY(check_ptr(stats, "stats"));
+    MGCT_TRY(check_ws(g, MGCT_WS_LANDWEBER, level, ws, bytes));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (o->storage) {
+        case MGCT_BF16: return learned_t<__nv_bfloat16>(g, level, vol, b, ws, *o, net, net_ws, net_bytes, stats, s);
+        case MGCT_F16: return learned_t<__half>(g, level, vol, b, ws, *o, net, net_ws, net_bytes, stats, s);
+        default: return learned_t<float>(g, level, vol, b, ws, *o, net, net_ws, net_bytes, stats, s);
+    }
+}
+
+int mgct_axpy(size_t count, float a, const float *x, float *y, mgct_stream stream) {
+    MGCT_TRY(check_ptr(x, "x"));
+    MGCT_TRY(check_ptr(y, "y"));
+    return launch_axpy(count, a, x, y, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

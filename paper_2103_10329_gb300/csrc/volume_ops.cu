@@ -358,6 +358,50 @@ int launch_em_update(size_t count, float *mu, const float *nd, double *part, cud
     return MGCT_OK;
 }
 
+// out = alpha * d, alpha read from a device scalar
+__global__ void k_scaled_copy(size_t count, const float *__restrict__ d, const double *__restrict__ alpha_p,
+                              float *__restrict__ out) {
+    const float alpha = (float)alpha_p[0];
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x)
+        out[t] = alpha * d[t];
+}
+
+int launch_scaled_copy(size_t count, const float *d, const double *alpha, float *out, cudaStream_t s) {
+    MGCT_KERNEL(KK_UPDATE, s, k_scaled_copy<<<grid_for(count), 256, 0, s>>>(count, d, alpha, out));
+    return MGCT_OK;
+}
+
+// mu <- S_lambda(mu + beta d') when the learned line search found beta > 0
+// (st[4] = beta, st[7] = non-finite flag), else mu <- S_lambda(mu + alpha d)
+// (st[0] = alpha): the plain step is the fallback.
+__global__ void k_update_choice(size_t count, float *__restrict__ mu, const float *__restrict__ d,
+                                const float *__restrict__ dl, const double *__restrict__ st, float lam) {
+    const bool learned = st[4] > 0.0 && st[7] == 0.0;
+    const float a = learned ? (float)st[4] : (float)st[0];
+    const float *__restrict__ dir = learned ? dl : d;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
+        float v = fmaf(a, dir[t], mu[t]);
+        if (lam > 0.0f) v = copysignf(fmaxf(fabsf(v) - lam, 0.0f), v);
+        mu[t] = v;
+    }
+}
+
+int launch_update_choice(size_t count, float *mu, const float *d, const float *dl, const double *st, float lam,
+                         cudaStream_t s) {
+    MGCT_KERNEL(KK_UPDATE, s, k_update_choice<<<grid_for(count), 256, 0, s>>>(count, mu, d, dl, st, lam));
+    return MGCT_OK;
+}
+
+__global__ void k_axpy(size_t count, float a, const float *__restrict__ x, float *__restrict__ y) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x)
+        y[t] = fmaf(a, x[t], y[t]);
+}
+
+int launch_axpy(size_t count, float a, const float *x, float *y, cudaStream_t s) {
+    MGCT_KERNEL(KK_UPDATE, s, k_axpy<<<grid_for(count), 256, 0, s>>>(count, a, x, y));
+    return MGCT_OK;
+}
+
 __global__ void k_fill(size_t count, float *__restrict__ x, float v) {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) x[t] = v;
 }

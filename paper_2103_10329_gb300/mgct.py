@@ -76,6 +76,12 @@ def lib():
     L.mgct_launch_count.restype = ctypes.c_uint64
     L.mgct_trace_enable.argtypes = [i]
     L.mgct_trace_read.argtypes = [vp, vp, i]
+    L.mgct_multigrid_coarse.argtypes = [vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp]
+    L.mgct_landweber_direction.argtypes = [vp, i, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp, vp]
+    L.mgct_landweber_learned.argtypes = [vp, i, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp, sz, vp, vp]
+    L.mgct_axpy.argtypes = [sz, ctypes.c_float, vp, vp, vp]
+    for fn in ("mgct_multigrid_coarse", "mgct_landweber_direction", "mgct_landweber_learned", "mgct_axpy"):
+        getattr(L, fn).restype = ctypes.c_int
     L.mgct_geometry_grad.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
     L.mgct_geometry_grad.restype = ctypes.c_int
     L.mgct_project_residual_static.argtypes = [vp, i, i, i, i, vp, vp, vp, vp, vp]
@@ -320,6 +326,54 @@ def multigrid_iteration(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, ws: 
     return vol
 
 
+def multigrid_coarse(geom: Geometry, vol: torch.Tensor, ws: torch.Tensor, n_subsets: int = 8,
+                     stats: torch.Tensor | None = None, storage=torch.float32, lam: float = 0.0):
+    o = _opts(None, lam, True, n_subsets, storage)
+    _check(lib().mgct_multigrid_coarse(geom.handle, _ptr(vol, "vol", torch.float32), _ptr(ws, "ws"), ws.numel(),
+                                       ctypes.byref(o), _ptr(stats, "stats", torch.float64), _stream()))
+    return vol
+
+
+def landweber_direction(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, level: int = 0,
+                        ws: torch.Tensor | None = None, out: torch.Tensor | None = None, precond: bool = True,
+                        stats: torch.Tensor | None = None, storage=torch.float32):
+    """The step alpha d of one Landweber step, without updating vol."""
+    if ws is None:
+        ws = workspace(geom, WS_LANDWEBER, level, vol.device)
+    if out is None:
+        out = torch.empty_like(vol)
+    o = _opts(None, 0.0, precond, 0, storage)
+    _check(lib().mgct_landweber_direction(geom.handle, level, _ptr(vol, "vol", torch.float32),
+                                          _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(), ctypes.byref(o),
+                                          _ptr(out, "out", torch.float32), _ptr(stats, "stats", torch.float64),
+                                          _stream()))
+    return out
+
+
+def landweber_learned(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, net: "Net", level: int = 0,
+                      ws: torch.Tensor | None = None, stats: torch.Tensor | None = None, storage=torch.float32,
+                      lam: float = 0.0):
+    """Learned Landweber step in place (mgct_landweber_learned); stats float64[8]."""
+    if ws is None:
+        ws = workspace(geom, WS_LANDWEBER, level, vol.device)
+    if stats is None:
+        stats = torch.zeros(8, dtype=torch.float64, device=vol.device)
+    nws = net._workspace(vol.numel(), False)
+    o = _opts(None, lam, True, 0, storage)
+    _check(lib().mgct_landweber_learned(geom.handle, level, _ptr(vol, "vol", torch.float32),
+                                        _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(), ctypes.byref(o),
+                                        net.handle, _ptr(nws, "net_ws"), nws.numel(),
+                                        _ptr(stats, "stats", torch.float64), _stream()))
+    return vol
+
+
+def axpy(a: float, x: torch.Tensor, y: torch.Tensor):
+    """y += a x (float32)."""
+    _check(lib().mgct_axpy(x.numel(), ctypes.c_float(a), _ptr(x, "x", torch.float32), _ptr(y, "y", torch.float32),
+                           _stream()))
+    return y
+
+
 class Reconstructor:
     """Alg. 1 driver state: a geometry with `levels` grids and its multigrid
     workspace.  `prepare(b)` once per data set, then `iterate(vol)`."""
@@ -343,6 +397,16 @@ class Reconstructor:
         for _ in range(iters):
             self.iterate(vol, **kw)
         return vol
+
+    def iterate_learned(self, vol: torch.Tensor, net: "Net", storage=torch.float32, n_subsets: int = 8):
+        """Alg. 1 with the learned Landweber step on grid 0 (coarse grids plain)."""
+        if self.geom.levels > 1:
+            multigrid_coarse(self.geom, vol, self.ws, n_subsets=n_subsets, stats=self.stats, storage=storage)
+        if not hasattr(self, "_lw_ws"):
+            self._lw_ws = workspace(self.geom, WS_LANDWEBER, 0, vol.device)
+            self.learned_stats = torch.zeros(8, dtype=torch.float64, device=vol.device)
+        return landweber_learned(self.geom, vol, self.b, net, ws=self._lw_ws, stats=self.learned_stats,
+                                 storage=storage)
 
 
 def project_residual_static(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, sumsq: torch.Tensor,

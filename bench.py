@@ -201,6 +201,29 @@ def make_workload(name, device="cuda"):
                 levels=L)
 
 
+def train_correction(phantoms: int, steps: int):
+    """The learned correction, trained on the GPU by the library's own kernels
+    on pairs the method generates on random 128^3 phantoms (192^2 detector,
+    360 views, 2 grids, 20 ellipsoids each)."""
+    import torch
+    from paper_2103_10329_gb300 import learned as LN
+    from paper_2103_10329_gb300 import mgct
+    t0 = time.perf_counter()
+    cases = [LN.make_case(128, 192, 360, 2, seed=20000 + i, count=20) for i in range(phantoms)]
+    pairs = LN.generate_pairs(cases, iters=2)
+    del cases
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = mgct.Net(seed=0)
+    hist = LN.train(net, pairs, steps=steps, crop=48, batch=4, lr=1e-3, log_every=max(1, steps // 10))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del pairs
+    return net, {"phantoms": phantoms, "pairs": 2 * phantoms, "steps": steps, "crop": 48, "batch": 4,
+                 "pair_generation_s": t1 - t0, "training_s": t2 - t1, "loss_log": hist,
+                 "config": "128^3, 192^2 detector, 360 views, 2 grids, 20 ellipsoids; Adam lr 1e-3"}
+
+
 def roi_rmse(vol, truth):
     import torch
     n = truth.shape[0]
@@ -446,14 +469,17 @@ def gpu_arm(args, rank, world):
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
 
-        def run_iters(storage, iters):
+        def run_iters(storage, iters, net=None):
             v = torch.zeros_like(vol)
             out = []
             tot = 0.0
             for _ in range(iters):
                 torch.cuda.synchronize()
                 s0.record()
-                rec.iterate(v, storage=storage)
+                if net is None:
+                    rec.iterate(v, storage=storage)
+                else:
+                    rec.iterate_learned(v, net, storage=storage)
                 s1.record()
                 torch.cuda.synchronize()
                 tot += s0.elapsed_time(s1)
@@ -473,8 +499,17 @@ def gpu_arm(args, rank, world):
                "E2_pmgl_fp32_2iter": e2, "pmgl_fp32_2iter_ms": base[-1][0],
                "sirt_2iter_ms": s0.elapsed_time(s1), "sirt_2iter_rmse_roi": roi_rmse(vs, truth),
                "forms": {}}
-        for name, st in (("fp32", torch.float32), ("bf16", torch.bfloat16), ("fp16", torch.float16)):
-            hist = run_iters(st, 3)
+        net = None
+        if not args.no_learned:
+            t0 = time.perf_counter()
+            net, train_info = train_correction(args.learn_phantoms, args.learn_steps)
+            train_info["wall_s"] = time.perf_counter() - t0
+            tta["learned_training"] = train_info
+        forms = [("fp32", torch.float32, False), ("bf16", torch.bfloat16, False), ("fp16", torch.float16, False)]
+        if net is not None:
+            forms += [("learned_fp32", torch.float32, True), ("learned_bf16", torch.bfloat16, True)]
+        for name, st, use_net in forms:
+            hist = run_iters(st, 3, net if use_net else None)
             reach = next(((i + 1, t) for i, (t, e) in enumerate(hist) if e <= e2 * (1 + 1e-3)), None)
             tta["forms"][name] = {"per_iter_ms_cum": [h[0] for h in hist], "per_iter_rmse_roi": [h[1] for h in hist],
                                   "iters_to_E2": reach[0] if reach else None,
@@ -514,6 +549,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-views", type=int, default=8)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learn-phantoms", type=int, default=48)
+    ap.add_argument("--learn-steps", type=int, default=1500)
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":

@@ -215,13 +215,13 @@ def train_correction(phantoms: int, steps: int):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     net = mgct.Net(seed=0)
-    hist = LN.train(net, pairs, steps=steps, crop=48, batch=4, lr=1e-3, log_every=max(1, steps // 10))
+    hist = LN.train(net, pairs, steps=steps, crop=64, batch=4, lr=1e-3, log_every=max(1, steps // 10))
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     del pairs
-    return net, {"phantoms": phantoms, "pairs": 2 * phantoms, "steps": steps, "crop": 48, "batch": 4,
+    return net, {"phantoms": phantoms, "pairs": 2 * phantoms, "steps": steps, "crop": 64, "batch": 4,
                  "pair_generation_s": t1 - t0, "training_s": t2 - t1, "loss_log": hist,
-                 "config": "128^3, 192^2 detector, 360 views, 2 grids, 20 ellipsoids; Adam lr 1e-3"}
+                 "config": "128^3, 192^2 detector, 360 views, 2 grids, 20 ellipsoids; Adam lr 1e-3, x0.3 after 70 %"}
 
 
 def roi_rmse(vol, truth):
@@ -550,8 +550,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-views", type=int, default=8)
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--learn-phantoms", type=int, default=48)
-    ap.add_argument("--learn-steps", type=int, default=1500)
+    ap.add_argument("--learn-phantoms", type=int, default=96)
+    ap.add_argument("--learn-steps", type=int, default=4000)
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":

@@ -49,9 +49,10 @@ def generate_pairs(cases, iters: int = 2, storage=torch.float32):
 
 
 def train(net: mgct.Net, pairs, steps: int = 300, crop: int = 32, batch: int = 4, lr: float = 1e-3,
-          seed: int = 0, log_every: int = 0):
-    """Adam on random crops; returns the loss history (host floats, one per
-    log interval)."""
+          seed: int = 0, log_every: int = 0, decay_at: float = 0.7, decay: float = 0.3):
+    """Adam on random crops, the learning rate multiplied by `decay` after
+    the fraction `decay_at` of the steps; returns the loss history (host
+    floats, one per log interval)."""
     g = torch.Generator(device="cpu").manual_seed(seed)
     n = pairs[0][0].shape[0]
     c = min(crop, n)
@@ -66,7 +67,7 @@ def train(net: mgct.Net, pairs, steps: int = 300, crop: int = 32, batch: int = 4
             x[j] = px[o[0]:o[0] + c, o[1]:o[1] + c, o[2]:o[2] + c]
             t[j] = pt[o[0]:o[0] + c, o[1]:o[1] + c, o[2]:o[2] + c]
         loss = net.forward_backward(x, t)
-        net.adam_step(lr)
+        net.adam_step(lr if it < decay_at * steps else lr * decay)
         if log_every and (it % log_every == 0 or it == steps - 1):
             hist.append(float(loss.item()))
     return hist

@@ -362,6 +362,9 @@ uint64_t mgct_launch_count(int reset);
 #define MGCT_TRACE_KINDS 10
 int mgct_trace_enable(int on);
 int mgct_trace_read(double *ms, uint64_t *launches, int nkinds);
+/* The same, restricted to launches made for grid `level` (solver steps and
+ * mgct_project / mgct_backproject tag their launches with their grid). */
+int mgct_trace_read_level(int level, double *ms, uint64_t *launches, int nkinds);
 
 #ifdef __cplusplus
 }

@@ -114,6 +114,7 @@ enum KernelKind {
 };
 void trace_begin(int kind, cudaStream_t s);
 void trace_end(int kind, cudaStream_t s);
+void trace_tag(int tag);  // grid level of the launches that follow (this thread)
 int check_ptr(const void *p, const char *name, bool may_be_null = false);
 
 #define MGCT_TRY(...)                   \

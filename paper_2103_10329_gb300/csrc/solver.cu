@@ -228,6 +228,7 @@ static int landweber_t(const mgct_geom *g, int level, float *mu, const float *b,
 template <typename ST>
 static int direction_t(const mgct_geom *g, int level, const float *mu, const float *b, void *ws, const mgct_lw_opts &o,
                        float *out, mgct_lw_stats *stats_out, cudaStream_t s) {
+    trace_tag(level);
     const LevelInfo &L = g->lev[level];
     Carver c(ws);
     LWSpace w = carve_lw(g, level, c);
@@ -247,6 +248,7 @@ static int direction_t(const mgct_geom *g, int level, const float *mu, const flo
 template <typename ST>
 static int learned_t(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
                      const mgct_net *net, void *net_ws, size_t net_bytes, double *stats, cudaStream_t s) {
+    trace_tag(level);
     const LevelInfo &L = g->lev[level];
     Carver c(ws);
     LWSpace w = carve_lw(g, level, c);
@@ -267,6 +269,7 @@ static int learned_t(const mgct_geom *g, int level, float *mu, const float *b, v
 
 static int landweber(const mgct_geom *g, int level, float *mu, const float *b, void *ws, const mgct_lw_opts &o,
                      mgct_lw_stats *stats_out, cudaStream_t s) {
+    trace_tag(level);
     switch (o.storage) {
         case MGCT_BF16: return landweber_t<__nv_bfloat16>(g, level, mu, b, ws, o, stats_out, s);
         case MGCT_F16: return landweber_t<__half>(g, level, mu, b, ws, o, stats_out, s);
@@ -276,6 +279,7 @@ static int landweber(const mgct_geom *g, int level, float *mu, const float *b, v
 
 static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *b, const float *pi, void *ws,
                   cudaStream_t s) {
+    trace_tag(level);
     const LevelInfo &L = g->lev[level];
     Carver c(ws);
     EMSpace w = carve_em(g, level, c);
@@ -296,6 +300,7 @@ static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *
 static int multigrid_level(const mgct_geom *g, int level, float *mu, const MGSpace &m, const float *b0,
                            const mgct_lw_opts &o, mgct_lw_stats *stats, cudaStream_t s, bool skip_landweber = false) {
     const int Lc = g->levels;
+    trace_tag(level);
     if (level + 1 < Lc) {
         const int nf = g->lev[level].n;
         float *mc = m.mu[level + 1], *oc = m.old[level + 1];
@@ -332,6 +337,7 @@ extern "C" {
 
 int mgct_project(const mgct_geom *g, int level, int view0, int nviews, int stride, const void *vol, mgct_dtype vt,
                  void *out, mgct_dtype ot, const float *b, double *sumsq, mgct_stream stream) {
+    trace_tag(level);
     MGCT_TRY(validate_level(g, level));
     MGCT_TRY(validate_views(g, view0, nviews, stride));
     MGCT_TRY(check_ptr(vol, "vol"));
@@ -382,6 +388,7 @@ int mgct_project(const mgct_geom *g, int level, int view0, int nviews, int strid
 
 int mgct_backproject(const mgct_geom *g, int level, int view0, int nviews, int stride, const void *sino,
                      mgct_dtype st, float *vol_out, int accumulate, mgct_stream stream) {
+    trace_tag(level);
     MGCT_TRY(validate_level(g, level));
     MGCT_TRY(validate_views(g, view0, nviews, stride));
     MGCT_TRY(check_ptr(sino, "sino", nviews == 0));

@@ -11,6 +11,7 @@ namespace mgct {
 namespace {
 struct Rec {
     int kind;
+    int tag;
     cudaEvent_t a, b;
 };
 std::mutex g_mu;
@@ -18,6 +19,7 @@ bool g_on = false;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 thread_local cudaEvent_t t_pending = nullptr;
+thread_local int t_tag = -1;
 
 cudaEvent_t get_event() {
     if (!g_pool.empty()) {
@@ -52,9 +54,11 @@ void trace_end(int kind, cudaStream_t s) {
     cudaEvent_t e = get_event();
     if (!e) return;
     cudaEventRecord(e, s);
-    g_recs.push_back({kind, t_pending, e});
+    g_recs.push_back({kind, t_tag, t_pending, e});
     t_pending = nullptr;
 }
+
+void trace_tag(int tag) { t_tag = tag; }
 
 }  // namespace mgct
 
@@ -69,7 +73,7 @@ int mgct_trace_enable(int on) {
     return MGCT_OK;
 }
 
-int mgct_trace_read(double *ms, uint64_t *launches, int nkinds) {
+static int trace_sum(int tag, double *ms, uint64_t *launches, int nkinds) {
     if (!ms || !launches || nkinds < 1) return set_error(MGCT_EINVAL, "ms and launches must not be NULL");
     std::lock_guard<std::mutex> lk(g_mu);
     for (int k = 0; k < nkinds; ++k) {
@@ -80,12 +84,19 @@ int mgct_trace_read(double *ms, uint64_t *launches, int nkinds) {
         MGCT_TRY(check_cuda(cudaEventSynchronize(r.b), "trace event sync"));
         float t = 0.0f;
         MGCT_TRY(check_cuda(cudaEventElapsedTime(&t, r.a, r.b), "trace elapsed time"));
-        if (r.kind >= 0 && r.kind < nkinds) {
+        if (r.kind >= 0 && r.kind < nkinds && (tag < 0 || r.tag == tag)) {
             ms[r.kind] += t;
             launches[r.kind] += 1;
         }
     }
     return MGCT_OK;
+}
+
+int mgct_trace_read(double *ms, uint64_t *launches, int nkinds) { return trace_sum(-1, ms, launches, nkinds); }
+
+int mgct_trace_read_level(int level, double *ms, uint64_t *launches, int nkinds) {
+    if (level < 0) return set_error(MGCT_EINVAL, "level must be >= 0");
+    return trace_sum(level, ms, launches, nkinds);
 }
 
 }  // extern "C"

@@ -76,6 +76,7 @@ def lib():
     L.mgct_launch_count.restype = ctypes.c_uint64
     L.mgct_trace_enable.argtypes = [i]
     L.mgct_trace_read.argtypes = [vp, vp, i]
+    L.mgct_trace_read_level.argtypes = [i, vp, vp, i]
     L.mgct_multigrid_coarse.argtypes = [vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp]
     L.mgct_landweber_direction.argtypes = [vp, i, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp, vp]
     L.mgct_landweber_learned.argtypes = [vp, i, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp, sz, vp, vp]
@@ -130,11 +131,15 @@ def trace_enable(on: bool = True):
     _check(lib().mgct_trace_enable(1 if on else 0))
 
 
-def trace_read() -> dict:
-    """{kind: (milliseconds, launches)} of the kernels traced since enable."""
+def trace_read(level: int | None = None) -> dict:
+    """{kind: (milliseconds, launches)} of the kernels traced since enable
+    (only those made for grid `level` when given)."""
     ms = (ctypes.c_double * len(TRACE_KINDS))()
     cnt = (ctypes.c_uint64 * len(TRACE_KINDS))()
-    _check(lib().mgct_trace_read(ms, cnt, len(TRACE_KINDS)))
+    if level is None:
+        _check(lib().mgct_trace_read(ms, cnt, len(TRACE_KINDS)))
+    else:
+        _check(lib().mgct_trace_read_level(int(level), ms, cnt, len(TRACE_KINDS)))
     return {k: (ms[i], int(cnt[i])) for i, k in enumerate(TRACE_KINDS)}
 
 

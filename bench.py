@@ -62,6 +62,21 @@ def workload_config(name):
             "l2": "inputs larger than L2 (sinogram %d MB)" % (w["views"] * w["nu"] ** 2 * 4 // 2 ** 20)}
 
 
+def aggregate(ms_local: float, units_local: float, device="cpu"):
+    """Whole-job timing over replicas: (max of ms over ranks, sum of units),
+    through torch.distributed when it is initialised (NCCL on the GPU machine,
+    gloo in the CPU tests), else the local values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, units_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def units_per_step(n, views, levels):
     """Voxel-view updates of the A / A^T calls of one multigrid iteration."""
     u = 0
@@ -386,8 +401,7 @@ def gpu_arm(args, rank, world):
     trace0 = mgct.trace_read(level=0)
     mgct.trace_enable(False)
     clk = clocks.stop()
-    ms_max = max_over_ranks(ms)
-    total_units = sum_over_ranks(units * args.steps)
+    ms_max, total_units = aggregate(ms, units * args.steps, dev)
     value = total_units / (ms_max / 1e3) / 1e9
 
     # ---- per-kernel work and the dominant kernel's roofline

@@ -195,7 +195,8 @@ typedef struct {
     double alpha;       /* step used (0 if |A d| = 0 or a non-finite value was met) */
     double r2;          /* |b - A mu|^2 before the step */
     double r2_pred;     /* |b - A (mu + alpha d)|^2 predicted by the line search */
-    double nonfinite;   /* 1 if a non-finite alpha was replaced by 0, else 0 */
+    double nonfinite;   /* 1 if a non-finite alpha was replaced by 0, else 0; with alpha = 0 the
+                           volume is left untouched */
 } mgct_lw_stats;
 
 /* One preconditioned Landweber step on grid `level` (Eq. 4; Eq. 2 when

@@ -292,6 +292,9 @@ int launch_step_size(const double *sums, const double *r2, double fixed_alpha, d
 __global__ void k_update(size_t count, float *__restrict__ mu, const float *__restrict__ d,
                          const double *__restrict__ alpha_p, float lam) {
     const float alpha = (float)alpha_p[0];
+    // alpha = 0 (no descent, or a non-finite step replaced by 0): leave mu
+    // untouched, even where d is not finite
+    if (alpha == 0.0f) return;
     const size_t n4 = count / 4;
     float4 *mu4 = reinterpret_cast<float4 *>(mu);
     const float4 *d4 = reinterpret_cast<const float4 *>(d);
@@ -379,6 +382,7 @@ __global__ void k_update_choice(size_t count, float *__restrict__ mu, const floa
     const bool learned = st[4] > 0.0 && st[7] == 0.0;
     const float a = learned ? (float)st[4] : (float)st[0];
     const float *__restrict__ dir = learned ? dl : d;
+    if (a == 0.0f) return;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count; t += (size_t)gridDim.x * blockDim.x) {
         float v = fmaf(a, dir[t], mu[t]);
         if (lam > 0.0f) v = copysignf(fmaxf(fabsf(v) - lam, 0.0f), v);

@@ -122,3 +122,26 @@ def test_multigrid_deterministic():
         rec.prepare(b)
         outs.append(rec.reconstruct(iters=2))
     assert torch.equal(outs[0], outs[1])
+
+
+def test_nonfinite_data_is_reported_and_leaves_mu_untouched():
+    """Failure detection without a GPU fault: a NaN in the data makes the
+    step size non-finite; the device stats flag it, alpha is replaced by 0
+    and the estimate is left exactly as it was."""
+    d = scan_desc(32, 48, 48, 12, 2104, levels=1)
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    ph, truth = phantom(32)
+    b = O.ellipsoid_line_integrals(og, ph).astype(np.float32)
+    b[3, 20, 20] = np.nan
+    mu = cuda(0.5 * truth)
+    before = mu.clone()
+    stats = torch.zeros(4, dtype=torch.float64, device="cuda")
+    mgct.landweber_step(g, mu, cuda(b), stats=stats)
+    s = stats.cpu().numpy()
+    assert s[3] == 1.0 and s[0] == 0.0
+    assert torch.equal(mu, before)
+    # clean data: no flag
+    b[3, 20, 20] = 0.0
+    mgct.landweber_step(g, mu, cuda(b), stats=stats)
+    assert stats[3].item() == 0.0 and stats[0].item() > 0.0

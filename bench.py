@@ -448,6 +448,9 @@ def gpu_arm(args, rank, world):
                 "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_clock:.0f} MHz",
                 "work": f"2 flop per nonzero of A, {nnz[0]:.4g} nonzeros per launch (4 bilinear taps per in-volume sample)",
                 "traffic": tr["bytes_per_launch"] if tr else None,
+                "l1_gather": {"bytes_per_launch": 4 * nnz[0], "peak_gbs": SMS * 128 * sm_clock * 1e6 / 1e9,
+                              "frac": 4 * nnz[0] / (avg_ms / 1e3) / (SMS * 128 * sm_clock * 1e6),
+                              "def": "one 4-byte on-chip load per nonzero against 128 B/clk/SM of L1"},
                 "hbm_bytes_alg": 4 * (n ** 3 + K * W["nu"] ** 2),
                 "hbm_frac_of_measured": 4 * (n ** 3 + K * W["nu"] ** 2) / (avg_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6790.0)}
     else:

@@ -28,6 +28,33 @@ __device__ __forceinline__ float tap(const VT *__restrict__ p, int off, bool ok)
     return ok ? to_f32(__ldg(p + off)) : 0.0f;
 }
 
+// Paired 16-bit volume (the mixed-precision solver path): entry e of a row
+// holds (V(e-1), V(e)) of the row's in-plane horizontal axis as one 32-bit
+// word, e = 0..n, with V(-1) = V(n) = 0, so both taps of a row come from one
+// aligned load.  Row length n + 1 words.
+template <typename T>
+struct Pair16 {};
+
+__device__ __forceinline__ float2 unpack2(uint32_t w, __nv_bfloat16) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+__device__ __forceinline__ float2 unpack2(uint32_t w, __half) {
+    __half2 h = *reinterpret_cast<__half2 *>(&w);
+    return __half22float2(h);
+}
+
+template <typename VT>
+struct VolTraits {
+    using elem = VT;
+    static constexpr bool paired = false;
+};
+template <typename T>
+struct VolTraits<Pair16<T>> {
+    using elem = uint32_t;
+    using half_t = T;
+    static constexpr bool paired = true;
+};
+
 // Block-wide float64 sum of up to two values; result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double *red) {
@@ -97,8 +124,9 @@ struct RaySum {
 
 template <typename VT>
 __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs &a, int ju, int jv,
-                                               const VT *__restrict__ vol,
-                                               const VT *__restrict__ volT) {
+                                               const typename VolTraits<VT>::elem *__restrict__ vol,
+                                               const typename VolTraits<VT>::elem *__restrict__ volT) {
+    using E = typename VolTraits<VT>::elem;
     const int n = a.n;
     const float ic = 0.5f * (float)(n - 1);
     const float up = (float)ju - 0.5f * (float)(a.nu - 1);
@@ -115,7 +143,7 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
     const DF rb = df_div(wb, wa), rz = df_div(wz, wa);  // slopes per plane
     const DF pb = df_div(nb, wa), pz = df_div(nz, wa);  // centred crossing at the central plane
     const float dl_h = sqrtf(fmaf(rz.hi, rz.hi, fmaf(rb.hi, rb.hi, 1.0f)));
-    const VT *__restrict__ base = d.ax ? vol : volT;
+    const E *__restrict__ base = d.ax ? vol : volT;
     float lo = 0.0f, hi = (float)(n - 1);
     clip_planes(pb.hi, rb.hi, ic, (float)n, lo, hi);
     clip_planes(pz.hi, rz.hi, ic, (float)n, lo, hi);
@@ -137,14 +165,30 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
             const float fb0 = floorf(gb), fz0 = floorf(gz);
             const float tb = gb - fb0, tz = gz - fz0;
             const int jb = Ib + (int)fb0, jz = Iz + (int)fz0;
-            const bool b0 = (unsigned)jb < (unsigned)n, b1 = (unsigned)(jb + 1) < (unsigned)n;
             const bool z0 = (unsigned)jz < (unsigned)n, z1 = (unsigned)(jz + 1) < (unsigned)n;
-            const int row0 = (jz * n + i) * n + jb;  // may be out of range; loads are predicated
-            const int row1 = row0 + n * n;
-            const float v00 = tap(base, row0, b0 && z0);
-            const float v10 = tap(base, row0 + 1, b1 && z0);
-            const float v01 = tap(base, row1, b0 && z1);
-            const float v11 = tap(base, row1 + 1, b1 && z1);
+            float v00, v10, v01, v11;
+            if constexpr (VolTraits<VT>::paired) {
+                // one word per row: entry jb + 1 = (V(jb), V(jb + 1))
+                const bool bok = (unsigned)(jb + 1) <= (unsigned)n;
+                const int row0 = (jz * n + i) * (n + 1) + jb + 1;
+                const int row1 = row0 + n * (n + 1);
+                const uint32_t w0 = (bok && z0) ? __ldg(base + row0) : 0u;
+                const uint32_t w1 = (bok && z1) ? __ldg(base + row1) : 0u;
+                const float2 p0 = unpack2(w0, typename VolTraits<VT>::half_t());
+                const float2 p1 = unpack2(w1, typename VolTraits<VT>::half_t());
+                v00 = p0.x;
+                v10 = p0.y;
+                v01 = p1.x;
+                v11 = p1.y;
+            } else {
+                const bool b0 = (unsigned)jb < (unsigned)n, b1 = (unsigned)(jb + 1) < (unsigned)n;
+                const int row0 = (jz * n + i) * n + jb;  // may be out of range; loads are predicated
+                const int row1 = row0 + n * n;
+                v00 = tap(base, row0, b0 && z0);
+                v10 = tap(base, row0 + 1, b1 && z0);
+                v01 = tap(base, row1, b0 && z1);
+                v11 = tap(base, row1 + 1, b1 && z1);
+            }
             const float a0 = fmaf(tb, v10 - v00, v00);
             const float a1 = fmaf(tb, v11 - v01, v01);
             part += fmaf(tz, a1 - a0, a0);
@@ -166,7 +210,8 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
 
 template <typename VT, typename Epi>
 __global__ void __launch_bounds__(PJ_BX *PJ_BY)
-    k_project(ProjArgs a, const VT *__restrict__ vol, const VT *__restrict__ volT, Epi epi) {
+    k_project(ProjArgs a, const typename VolTraits<VT>::elem *__restrict__ vol,
+              const typename VolTraits<VT>::elem *__restrict__ volT, Epi epi) {
     __shared__ ViewGeom G;
     const int vtiles = (a.nv + PJ_BY - 1) / PJ_BY;
     const int group = blockIdx.z / vtiles, vt = blockIdx.z % vtiles;
@@ -180,7 +225,7 @@ __global__ void __launch_bounds__(PJ_BX *PJ_BY)
     const int jv = vt * PJ_BY + threadIdx.y;
     const bool active = view_ok && ju < a.nu && jv < a.nv;
     RaySum rs{0.0f, 0.0f};
-    if (active) rs = ray_integral(G, a, ju, jv, vol, volT);
+    if (active) rs = ray_integral<VT>(G, a, ju, jv, vol, volT);
     epi(i, k, jv, ju, active, rs.acc, rs.dlh);
 }
 
@@ -274,8 +319,9 @@ struct EpiEMTerms {
 };
 
 template <typename VT, typename Epi>
-int launch_project(const mgct_geom *g, int level, int view0, int nviews, int stride, const VT *vol,
-                   const VT *volT, const Epi &epi, cudaStream_t s, int *nblocks = nullptr) {
+int launch_project(const mgct_geom *g, int level, int view0, int nviews, int stride,
+                   const typename VolTraits<VT>::elem *vol, const typename VolTraits<VT>::elem *volT,
+                   const Epi &epi, cudaStream_t s, int *nblocks = nullptr) {
     const LevelInfo &L = g->lev[level];
     ProjArgs a;
     a.views = L.d_views;

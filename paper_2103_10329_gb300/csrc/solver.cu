@@ -26,6 +26,8 @@ int launch_scaled_copy(size_t count, const float *d, const double *alpha, float 
 int launch_update_choice(size_t count, float *mu, const float *d, const float *dl, const double *st, float lam,
                          cudaStream_t s);
 int launch_axpy(size_t count, float a, const float *x, float *y, cudaStream_t s);
+template <typename T>
+int launch_cast_pairs(int n, const float *in, uint32_t *py, uint32_t *px, cudaStream_t s);
 
 int launch_column_table(const mgct_geom *g, int level, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
@@ -61,6 +63,7 @@ static size_t proj_blocks(const mgct_geom *g, const LevelInfo &L) {
 
 struct LWSpace {
     float *r, *grad, *d, *muT;
+    uint32_t *pairs;              // paired 16-bit projector input, two layouts of n^2 (n+1) words
     double *part, *sums, *stats;  // sums: [0] r2, [1] <r,Ad>, [2] |Ad|^2 ; stats: 4
 };
 
@@ -71,6 +74,7 @@ static LWSpace carve_lw(const mgct_geom *g, int level, Carver &c) {
     w.grad = c.take<float>(vox(L));
     w.d = c.take<float>(vox(L));
     w.muT = c.take<float>(vox(L));
+    w.pairs = c.take<uint32_t>(2 * (size_t)L.n * L.n * (L.n + 1));
     w.part = c.take<double>(2 * proj_blocks(g, L) + 64);
     w.sums = c.take<double>(8);
     w.stats = c.take<double>(8);
@@ -157,22 +161,19 @@ static int lw_direction(const mgct_geom *g, int level, const float *mu, const fl
     const size_t nv3 = vox(L);
     constexpr bool F32 = std::is_same<ST, float>::value;
     MGCT_TRY(check_cuda(cudaMemsetAsync(w.sums, 0, 8 * sizeof(double), s), "memset"));
-    const ST *muS;
-    const ST *muST;
-    if constexpr (F32) {
-        MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
-        muS = mu;
-        muST = w.muT;
-    } else {
-        ST *a = reinterpret_cast<ST *>(w.muT);
-        MGCT_TRY(launch_cast_transpose<ST>(L.n, mu, a, a + nv3, s));
-        muS = a;
-        muST = a + nv3;
-    }
     ST *r = reinterpret_cast<ST *>(w.r);
     int nb = 0;
     EpiResidual<ST, true> er{r, b, w.part, L.nu, L.nv, K};
-    MGCT_TRY(launch_project<ST>(g, level, 0, K, 1, muS, muST, er, s, &nb));
+    if constexpr (F32) {
+        MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
+        MGCT_TRY(launch_project<float>(g, level, 0, K, 1, mu, w.muT, er, s, &nb));
+    } else {
+        // paired 16-bit shadows of mu: two taps per load
+        const size_t half = (size_t)L.n * L.n * (L.n + 1);
+        MGCT_TRY(launch_cast_pairs<ST>(L.n, mu, w.pairs, w.pairs + half, s));
+        MGCT_TRY(launch_project<Pair16<ST>>(g, level, 0, K, 1, w.pairs, w.pairs + half, er, s, &nb));
+    }
+    (void)nv3;
     MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
     MGCT_TRY(launch_backproject<1, ST, true>(g, level, 0, K, 1, r, w.grad, 0, s));
     *d_out = w.grad;
@@ -191,21 +192,18 @@ static int lw_line_search(const mgct_geom *g, int level, const float *dir, float
     const LevelInfo &L = g->lev[level];
     const int K = g->desc.n_views;
     const size_t nv3 = vox(L);
-    const ST *dS;
-    const ST *dST;
-    if constexpr (std::is_same<ST, float>::value) {
-        MGCT_TRY(launch_transpose_xy<float>(L.n, dir, spare, s));
-        dS = dir;
-        dST = spare;
-    } else {
-        ST *a = reinterpret_cast<ST *>(spare);
-        MGCT_TRY(launch_cast_transpose<ST>(L.n, dir, a, a + nv3, s));
-        dS = a;
-        dST = a + nv3;
-    }
     int nb = 0;
     EpiDualDot<ST> ed{reinterpret_cast<ST *>(w.r), w.part, L.nu, L.nv, K};
-    MGCT_TRY(launch_project<ST>(g, level, 0, K, 1, dS, dST, ed, s, &nb));
+    if constexpr (std::is_same<ST, float>::value) {
+        MGCT_TRY(launch_transpose_xy<float>(L.n, dir, spare, s));
+        MGCT_TRY(launch_project<float>(g, level, 0, K, 1, dir, spare, ed, s, &nb));
+    } else {
+        const size_t half = (size_t)L.n * L.n * (L.n + 1);
+        MGCT_TRY(launch_cast_pairs<ST>(L.n, dir, w.pairs, w.pairs + half, s));
+        MGCT_TRY(launch_project<Pair16<ST>>(g, level, 0, K, 1, w.pairs, w.pairs + half, ed, s, &nb));
+    }
+    (void)nv3;
+    (void)spare;
     return launch_sum_partials(w.part, nb, 2, w.sums + slot, s);
 }
 

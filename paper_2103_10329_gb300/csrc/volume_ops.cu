@@ -72,6 +72,66 @@ template int launch_cast_transpose<__nv_bfloat16>(int, const float *, __nv_bfloa
 template int launch_cast_transpose<__half>(int, const float *, __half *, __half *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// float32 vol [z][y][x] -> paired 16-bit rows for the projector:
+//   Py[z][y][e] = (V[z][y][e-1], V[z][y][e])   (y-major rays, pairs along x)
+//   Px[z][x][e] = (V[z][e-1][x], V[z][e][x])   (x-major rays, pairs along y)
+// e = 0..n, zero outside [0, n-1]; rows of n + 1 words.  One pass through a
+// 34 x 34 shared tile (the 32 x 32 block plus a one-voxel halo).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack2(float lo, float hi, __nv_bfloat16) {
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+__device__ __forceinline__ uint32_t pack2(float lo, float hi, __half) {
+    const uint32_t a = __half_as_ushort(__float2half_rn(lo));
+    const uint32_t b = __half_as_ushort(__float2half_rn(hi));
+    return a | (b << 16);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cast_pairs(int n, const float *__restrict__ in, uint32_t *__restrict__ py,
+                                                    uint32_t *__restrict__ px) {
+    __shared__ float tile[34][35];  // [y - y0 + 1][x - x0 + 1]
+    const int z = blockIdx.z;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const size_t slab = (size_t)z * n * n;
+    for (int t = threadIdx.x + 32 * threadIdx.y; t < 34 * 34; t += 256) {
+        const int ty = t / 34, tx = t % 34;
+        const int y = y0 + ty - 1, x = x0 + tx - 1;
+        tile[ty][tx] = (x >= 0 && x < n && y >= 0 && y < n) ? in[slab + (size_t)y * n + x] : 0.0f;
+    }
+    __syncthreads();
+    const size_t prow = (size_t)(n + 1);
+    // entries e = x0 .. x0 + 31 of rows y (plus e = n in the last column block)
+    for (int dy = threadIdx.y; dy < 32; dy += 8) {
+        const int y = y0 + dy;
+        if (y >= n) break;
+        const int e = x0 + threadIdx.x;
+        if (e <= n) py[(slab / n + y) * prow + e] = pack2(tile[dy + 1][threadIdx.x], tile[dy + 1][threadIdx.x + 1], T());
+        if (threadIdx.x == 31 && e + 1 == n)
+            py[(slab / n + y) * prow + n] = pack2(tile[dy + 1][32], 0.0f, T());
+    }
+    for (int dx = threadIdx.y; dx < 32; dx += 8) {
+        const int x = x0 + dx;
+        if (x >= n) break;
+        const int e = y0 + threadIdx.x;
+        if (e <= n) px[((size_t)z * n + x) * prow + e] = pack2(tile[threadIdx.x][dx + 1], tile[threadIdx.x + 1][dx + 1], T());
+        if (threadIdx.x == 31 && e + 1 == n)
+            px[((size_t)z * n + x) * prow + n] = pack2(tile[32][dx + 1], 0.0f, T());
+    }
+}
+
+template <typename T>
+int launch_cast_pairs(int n, const float *in, uint32_t *py, uint32_t *px, cudaStream_t s) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32, n);
+    MGCT_KERNEL(KK_TRANSPOSE, s, k_cast_pairs<T><<<grid, dim3(32, 8), 0, s>>>(n, in, py, px));
+    return MGCT_OK;
+}
+template int launch_cast_pairs<__nv_bfloat16>(int, const float *, uint32_t *, uint32_t *, cudaStream_t);
+template int launch_cast_pairs<__half>(int, const float *, uint32_t *, uint32_t *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Eq. 5 stencil: out = p * in, zero padding.  Block = 32 x 8 columns; each
 // thread walks ZB planes along z with three rolling halo planes in shared
 // memory, so every input element is read from HBM about once.
@@ -270,14 +330,20 @@ int launch_sum_partials(const double *part, int count, int nvals, double *out, c
 __global__ void k_step_size(const double *__restrict__ sums, const double *__restrict__ r2, double fixed_alpha,
                             double *__restrict__ stats) {
     double num = sums[0], den = sums[1];
+    double rr = r2 ? r2[0] : 0.0;
     double alpha, nonfinite = 0.0;
-    if (fixed_alpha > 0.0) alpha = fixed_alpha;
-    else alpha = den > 0.0 ? num / den : 0.0;
-    if (!isfinite(alpha)) {
+    if (!isfinite(num) || !isfinite(den) || !isfinite(rr)) {
+        // a non-finite residual or direction: no step
         alpha = 0.0;
         nonfinite = 1.0;
+    } else {
+        if (fixed_alpha > 0.0) alpha = fixed_alpha;
+        else alpha = den > 0.0 ? num / den : 0.0;
+        if (!isfinite(alpha)) {
+            alpha = 0.0;
+            nonfinite = 1.0;
+        }
     }
-    double rr = r2 ? r2[0] : 0.0;
     stats[0] = alpha;
     stats[1] = rr;
     stats[2] = rr - 2.0 * alpha * num + alpha * alpha * den;

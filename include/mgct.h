@@ -267,8 +267,9 @@ int mgct_geometry_grad(const mgct_geom *geom, int level, int view0, int nviews, 
  * correction on top of it).
  *
  * Network f: four 3x3x3 convolutions at full resolution (zero padding),
- * 1 -> 16 -> 32 -> 64 -> 1 channels, ReLU after the first three, on BF16
- * tensor cores with float32 accumulation and BF16 activations; float32
+ * 1 -> 16 -> 32 -> 64 -> 1 channels, ReLU after the first three, on the BF16
+ * tensor cores (tcgen05, accumulators in tensor memory) with float32
+ * accumulation and BF16 activations; float32
  * master weights trained by Adam.  Volumes are [B][D][H][W] float32, B
  * volumes of D x H x W voxels, B*D*H*W < 2^31.
  *
@@ -300,6 +301,13 @@ int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const f
                               const float *t, void *workspace, size_t ws_bytes, double *loss,
                               mgct_stream stream);
 int mgct_net_adam_step(mgct_net *net, double lr, mgct_stream stream);
+/* The convolutions run on the tcgen05 tensor cores and wait on their MMAs
+ * with bounded waits; when a wait expires the kernel records it in a device
+ * word of the net, skips its stores and returns.  The pass's results are
+ * then NaN (mgct_net_apply's output, mgct_net_forward_backward's loss).
+ * mgct_net_check synchronises `stream`, clears the word and returns
+ * MGCT_ETIMEOUT if it was set, MGCT_OK otherwise. */
+int mgct_net_check(const mgct_net *net, mgct_stream stream);
 
 /* Learned Landweber step on grid `level`: the plain step alpha d (Eq. 4 with
  * the exact line search), the corrected step d' = mgct_net_apply(alpha d),

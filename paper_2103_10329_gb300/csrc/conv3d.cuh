@@ -9,9 +9,9 @@
 //                 = the forward with weights wT[26 - tap][ci][co]
 //   weight grad:  dw[tap][co][ci] = sum_p gout[p][co] in[p + tap][ci]
 //
-// GEMM tiles use mma.sync m16n8k16 (bf16 x bf16 -> f32): A fragments are
-// rows = voxels, k = input channels of one tap; B fragments k = input
-// channels, n = output channels.
+// This header holds the shared argument block and the weight gradient
+// (mma.sync m16n8k16, bf16 x bf16 -> f32); the forward and backward-data
+// convolutions run on tcgen05 (conv3d_tc.cuh).
 #pragma once
 
 #include "common.cuh"
@@ -50,97 +50,6 @@ __device__ __forceinline__ void decode_voxel(int p, int W, int H, int D, int &b,
 }
 
 constexpr int CV_M = 128;  // voxels per block (4 warps x 2 m16 tiles)
-
-template <int CIN, int COUT, bool RELU, bool OUT_F32>
-__global__ void __launch_bounds__(128) k_conv_fwd(ConvArgs a) {
-    static_assert(CIN % 16 == 0 && COUT % 8 == 0, "channel padding");
-    constexpr int AP = CIN + 8, BP = CIN + 8;  // padded smem rows (bank spread)
-    __shared__ __align__(16) __nv_bfloat16 As[CV_M][AP];
-    __shared__ __align__(16) __nv_bfloat16 Bs[COUT][BP];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t4 = lane & 3;
-    const int p0 = blockIdx.x * CV_M;
-    float acc[2][COUT / 8][4];
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int nt = 0; nt < COUT / 8; ++nt)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[m][nt][q] = 0.0f;
-    for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        __syncthreads();
-        // gather the A tile: CV_M voxels x CIN channels, shifted by the tap
-        for (int idx = tid; idx < CV_M * (CIN / 8); idx += 128) {
-            const int r = idx / (CIN / 8), ch = idx % (CIN / 8);
-            const int p = p0 + r;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (p < a.nvox) {
-                int b, z, y, x;
-                decode_voxel(p, a.W, a.H, a.D, b, z, y, x);
-                z += dz;
-                y += dy;
-                x += dx;
-                if ((unsigned)z < (unsigned)a.D && (unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W) {
-                    const size_t q = (((size_t)b * a.D + z) * a.H + y) * a.W + x;
-                    v = *reinterpret_cast<const uint4 *>(a.in + q * CIN + ch * 8);
-                }
-            }
-            *reinterpret_cast<uint4 *>(&As[r][ch * 8]) = v;
-        }
-        for (int idx = tid; idx < COUT * (CIN / 8); idx += 128) {
-            const int co = idx / (CIN / 8), ch = idx % (CIN / 8);
-            *reinterpret_cast<uint4 *>(&Bs[co][ch * 8]) =
-                *reinterpret_cast<const uint4 *>(a.w + ((size_t)tap * COUT + co) * CIN + ch * 8);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                const int r0 = warp * 32 + m * 16;
-                af[m][0] = ld_u32(&As[r0 + g][kc * 16 + 2 * t4]);
-                af[m][1] = ld_u32(&As[r0 + g + 8][kc * 16 + 2 * t4]);
-                af[m][2] = ld_u32(&As[r0 + g][kc * 16 + 2 * t4 + 8]);
-                af[m][3] = ld_u32(&As[r0 + g + 8][kc * 16 + 2 * t4 + 8]);
-            }
-#pragma unroll
-            for (int nt = 0; nt < COUT / 8; ++nt) {
-                uint32_t bf[2];
-                bf[0] = ld_u32(&Bs[nt * 8 + g][kc * 16 + 2 * t4]);
-                bf[1] = ld_u32(&Bs[nt * 8 + g][kc * 16 + 2 * t4 + 8]);
-#pragma unroll
-                for (int m = 0; m < 2; ++m) mma_bf16_16816(acc[m][nt], af[m], bf);
-            }
-        }
-    }
-    // epilogue: bias, ReLU, mask, store
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-#pragma unroll
-        for (int hr = 0; hr < 2; ++hr) {
-            const int p = p0 + warp * 32 + m * 16 + g + hr * 8;
-            if (p >= a.nvox) continue;
-#pragma unroll
-            for (int nt = 0; nt < COUT / 8; ++nt) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int co = nt * 8 + 2 * t4 + j;
-                    if (co >= a.out_ch) continue;
-                    float v = acc[m][nt][hr * 2 + j] + (a.bias ? a.bias[co] : 0.0f);
-                    if (RELU) v = fmaxf(v, 0.0f);
-                    if (a.mask && !(__bfloat162float(a.mask[(size_t)p * COUT + co]) > 0.0f)) v = 0.0f;
-                    if (OUT_F32) {
-                        static_cast<float *>(a.out)[p] = v;  // channel 0 only
-                    } else {
-                        static_cast<__nv_bfloat16 *>(a.out)[(size_t)p * a.out_stride + co] = __float2bfloat16_rn(v);
-                    }
-                }
-            }
-        }
-    }
-}
 
 // Weight gradient, one tap per blockIdx.y; each block loops over voxel tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ... and writes its partial

@@ -14,7 +14,7 @@
 #include <vector>
 
 #include "common.cuh"
-#include "conv3d.cuh"
+#include "conv3d_tc.cuh"
 
 namespace mgct {
 
@@ -38,6 +38,7 @@ struct mgct_net {
     __nv_bfloat16 *wf[mgct::NL];           // bf16 forward weights
     __nv_bfloat16 *wt[mgct::NL];           // bf16 backward-data weights [26 - tap][CIN][COUT]
     double *loss;                          // device scalar of the last forward_backward
+    int *err;                              // device word: a convolution's bounded wait expired
     int64_t step;
 };
 
@@ -75,18 +76,21 @@ __global__ void k_net_input(const float *__restrict__ x, const double *__restric
 }
 
 // out = s (x + y)  (the corrected step in the caller's units)
+// (NaN everywhere when a convolution of this pass failed, so that the
+// learned step's line search rejects it)
 __global__ void k_net_output(const float *__restrict__ x, const float *__restrict__ y, const double *__restrict__ sumsq,
-                             int nvox, float *__restrict__ out) {
-    const float s = (float)fmax(sqrt(sumsq[0] / (double)nvox), 1e-30);
+                             int nvox, const int *__restrict__ err, float *__restrict__ out) {
+    const float s = *err ? __int_as_float(0x7fc00000) : (float)fmax(sqrt(sumsq[0] / (double)nvox), 1e-30);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nvox; p += gridDim.x * blockDim.x)
         out[p] = s * (x[p] + y[p]);
 }
 
 // loss partials and the output gradient: r = x + y - t; dL/dy = 2 r / N
+// (a NaN loss when a convolution of the forward pass failed)
 __global__ void k_mse(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ t, int nvox,
-                      __nv_bfloat16 *__restrict__ gy, double *__restrict__ part) {
+                      const int *__restrict__ err, __nv_bfloat16 *__restrict__ gy, double *__restrict__ part) {
     __shared__ double red[256];
-    double s = 0.0;
+    double s = *err ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
     const float sc = 2.0f / (float)nvox;
     const double inv_n = 1.0 / (double)nvox;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nvox; p += gridDim.x * blockDim.x) {
@@ -164,27 +168,45 @@ __global__ void k_adam(int n, float *__restrict__ w, const float *__restrict__ g
 // ---------------------------------------------------------------------------
 // launch helpers (dispatch over the fixed layer shapes)
 // ---------------------------------------------------------------------------
+// persistent launch of the brick kernel: one block per SM times the blocks
+// that fit (shared memory, and the 512 tensor-memory columns of an SM)
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
-static int conv_fwd_t(const ConvArgs &a, cudaStream_t s) {
-    MGCT_KERNEL(KK_CONV, s, k_conv_fwd<CIN, COUT, RELU, OUT_F32><<<(a.nvox + CV_M - 1) / CV_M, 128, 0, s>>>(a));
+static int conv_fwd_t(const ConvArgs &a, int *err, cudaStream_t s) {
+    using C = BrickCfg<CIN, COUT>;
+    auto kern = k_conv_brick_tc<CIN, COUT, RELU, OUT_F32>;
+    static int per_sm = 0, nsm = 0;  // per instantiation
+    if (!per_sm) {
+        MGCT_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM),
+                            "conv smem"));
+        int dev = 0, occ = 0;
+        MGCT_TRY(check_cuda(cudaGetDevice(&dev), "conv device"));
+        MGCT_TRY(check_cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "conv SMs"));
+        MGCT_TRY(check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, C::SMEM), "conv occupancy"));
+        if (occ < 1) return set_error(MGCT_ECUDA, "convolution does not fit on an SM");
+        per_sm = std::min(occ, (int)(512 / C::NCOLS));
+    }
+    const int ntiles = brick_tiles(a.B, a.D, a.H, a.W).ntiles;
+    if (ntiles == 0) return MGCT_OK;
+    const int grid = std::min(ntiles, nsm * per_sm);
+    MGCT_KERNEL(KK_CONV, s, kern<<<grid, 128, C::SMEM, s>>>(a, err));
     return MGCT_OK;
 }
 
-static int conv_forward(int l, const ConvArgs &a, cudaStream_t s) {
+static int conv_forward(int l, const ConvArgs &a, int *err, cudaStream_t s) {
     switch (l) {
-        case 0: return conv_fwd_t<16, 16, true, false>(a, s);
-        case 1: return conv_fwd_t<16, 32, true, false>(a, s);
-        case 2: return conv_fwd_t<32, 64, true, false>(a, s);
-        default: return conv_fwd_t<64, 16, false, true>(a, s);
+        case 0: return conv_fwd_t<16, 16, true, false>(a, err, s);
+        case 1: return conv_fwd_t<16, 32, true, false>(a, err, s);
+        case 2: return conv_fwd_t<32, 64, true, false>(a, err, s);
+        default: return conv_fwd_t<64, 16, false, true>(a, err, s);
     }
 }
 
 // backward data of layer l: forward shape (CIN' = COUT_l, COUT' = CIN_l)
-static int conv_bwd_data(int l, const ConvArgs &a, cudaStream_t s) {
+static int conv_bwd_data(int l, const ConvArgs &a, int *err, cudaStream_t s) {
     switch (l) {
-        case 1: return conv_fwd_t<32, 16, false, false>(a, s);
-        case 2: return conv_fwd_t<64, 32, false, false>(a, s);
-        case 3: return conv_fwd_t<16, 64, false, false>(a, s);
+        case 1: return conv_fwd_t<32, 16, false, false>(a, err, s);
+        case 2: return conv_fwd_t<64, 32, false, false>(a, err, s);
+        case 3: return conv_fwd_t<16, 64, false, false>(a, err, s);
         default: return set_error(MGCT_EINVAL, "no data gradient for the input layer");
     }
 }
@@ -275,6 +297,7 @@ void mgct_net_destroy(mgct_net *net) {
             if (p) cudaFree(p);
     }
     if (net->loss) cudaFree(net->loss);
+    if (net->err) cudaFree(net->err);
     delete net;
 }
 
@@ -354,6 +377,8 @@ int mgct_net_create(uint64_t seed, mgct_net **out) {
         }
     }
     if (!st) st = check_cuda(cudaMalloc(&net->loss, 8), "net alloc");
+    if (!st) st = check_cuda(cudaMalloc(&net->err, sizeof(int)), "net alloc");
+    if (!st) st = check_cuda(cudaMemset(net->err, 0, sizeof(int)), "net alloc");
     if (st) {
         mgct_net_destroy(net);
         return st;
@@ -412,7 +437,7 @@ static int net_forward(const mgct_net *net, int B, int D, int H, int W, const fl
             a.out_ch = 1;
             a.out_stride = 1;
         }
-        MGCT_TRY(conv_forward(l, a, s));
+        MGCT_TRY(conv_forward(l, a, net->err, s));
         if (l < NL - 1) cur = sp.act[l];
     }
     return MGCT_OK;
@@ -460,7 +485,7 @@ int mgct_net_apply(const mgct_net *net, int B, int D, int H, int W, const float 
     carve_net(nvox, false, static_cast<char *>(ws), &sp);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     MGCT_TRY(net_forward(net, B, D, H, W, dir, true, sp, s));
-    MGCT_KERNEL(KK_CONV, s, k_net_output<<<std::min((int)((nvox + 255) / 256), 152 * 32), 256, 0, s>>>(sp.xs, sp.y, sp.sumsq, (int)nvox, out));
+    MGCT_KERNEL(KK_CONV, s, k_net_output<<<std::min((int)((nvox + 255) / 256), 152 * 32), 256, 0, s>>>(sp.xs, sp.y, sp.sumsq, (int)nvox, net->err, out));
     return MGCT_OK;
 }
 
@@ -481,7 +506,7 @@ int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const f
     // x and t are already in scaled units
     MGCT_TRY(net_forward(net, B, D, H, W, x, false, sp, s));
     const int nb = std::min(1024, (nvox + 255) / 256);
-    MGCT_KERNEL(KK_CONV, s, k_mse<<<nb, 256, 0, s>>>(sp.xs, sp.y, t, nvox, sp.g[NL - 1], sp.lpart));
+    MGCT_KERNEL(KK_CONV, s, k_mse<<<nb, 256, 0, s>>>(sp.xs, sp.y, t, nvox, net->err, sp.g[NL - 1], sp.lpart));
     MGCT_TRY(launch_sum_partials(sp.lpart, nb, 1, net->loss, s));
     // backward through the layers; g[l] = dL/d(output of layer l)
     for (int l = NL - 1; l >= 0; --l) {
@@ -506,11 +531,22 @@ int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const f
             a.nvox = nvox;
             a.out_ch = LCIN[l];
             a.out_stride = LCIN[l];
-            MGCT_TRY(conv_bwd_data(l, a, s));
+            MGCT_TRY(conv_bwd_data(l, a, net->err, s));
         }
     }
     if (loss) MGCT_TRY(check_cuda(cudaMemcpyAsync(loss, net->loss, 8, cudaMemcpyDeviceToDevice, s), "loss copy"));
     return MGCT_OK;
+}
+
+int mgct_net_check(const mgct_net *net, mgct_stream stream) {
+    if (!net) return set_error(MGCT_EINVAL, "net is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int flag = 0;
+    MGCT_TRY(check_cuda(cudaMemcpyAsync(&flag, net->err, sizeof(int), cudaMemcpyDeviceToHost, s), "net check"));
+    MGCT_TRY(check_cuda(cudaStreamSynchronize(s), "net check"));
+    if (!flag) return MGCT_OK;
+    MGCT_TRY(check_cuda(cudaMemsetAsync(net->err, 0, sizeof(int), s), "net check"));
+    return set_error(MGCT_ETIMEOUT, "a tensor-core convolution gave up waiting for its MMAs");
 }
 
 int mgct_net_adam_step(mgct_net *net, double lr, mgct_stream stream) {

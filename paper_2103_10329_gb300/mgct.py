@@ -454,8 +454,9 @@ def _net_sigs():
     L.mgct_net_apply.argtypes = [vp, i, i, i, i, vp, vp, vp, sz, vp]
     L.mgct_net_forward_backward.argtypes = [vp, i, i, i, i, vp, vp, vp, sz, vp, vp]
     L.mgct_net_adam_step.argtypes = [vp, ctypes.c_double, vp]
+    L.mgct_net_check.argtypes = [vp, vp]
     for fn in ("mgct_net_create", "mgct_net_set_params", "mgct_net_get_params", "mgct_net_get_grads",
-               "mgct_net_apply", "mgct_net_forward_backward", "mgct_net_adam_step"):
+               "mgct_net_apply", "mgct_net_forward_backward", "mgct_net_adam_step", "mgct_net_check"):
         getattr(L, fn).restype = ctypes.c_int
     _net_sigs_done = True
     return L
@@ -514,6 +515,11 @@ class Net:
 
     def adam_step(self, lr: float) -> None:
         _check(_net_sigs().mgct_net_adam_step(self.handle, float(lr), _stream()))
+
+    def check(self) -> None:
+        """Synchronise and raise if a convolution's bounded wait expired
+        (mgct_net_check)."""
+        _check(_net_sigs().mgct_net_check(self.handle, _stream()))
 
     def close(self):
         if getattr(self, "handle", None):

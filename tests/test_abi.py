@@ -58,3 +58,4 @@ def test_host_side_argument_checks(L):
     desc = mgct.GeomDesc(64, 96, 96, 0, 2, 2.0, 4.0, 0.02, None, None, None, 2)
     assert L.mgct_geometry_create(ctypes.byref(desc), ctypes.byref(h)) == -1
     assert L.mgct_workspace_bytes(None, 0, 0) == 0
+    assert L.mgct_net_check(None, None) == -1

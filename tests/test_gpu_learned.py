@@ -57,6 +57,7 @@ def test_forward_vs_oracle(shape):
     net.set_params(p)
     step = 0.01 * np.random.default_rng(6).standard_normal(shape)
     out = to_np(net.apply(torch.tensor(step, dtype=torch.float32, device="cuda")))
+    net.check()
     s = np.sqrt(np.mean(step.astype(np.float32).astype(np.float64) ** 2))
     x = step.astype(np.float32).astype(np.float64) / s
     y_bf, _ = NL.forward(p.astype(np.float64), x, bf=True)
@@ -65,6 +66,40 @@ def test_forward_vs_oracle(shape):
     scale = np.abs(y_64).max()
     assert np.abs(y_gpu - y_bf).max() <= 8 * U * scale
     assert np.abs(y_gpu - y_64).max() <= 32 * U * scale
+
+
+@pytest.mark.parametrize("shape", [(2, 20, 70, 45), (1, 256, 256, 256)])
+def test_forward_sampled_large(shape):
+    """Volumes of many brick tiles (ragged in every axis; up to the 256^3
+    grid the correction runs on), checked at sampled voxels: the four 3x3x3
+    layers see the input within 4 voxels, so the oracle on the 9^3 crop
+    around a voxel (cut at the volume's own faces, where the zero padding is
+    the same) gives that voxel's output exactly."""
+    from paper_2103_10329_gb300 import mgct
+    net = mgct.Net()
+    p = random_params(21)
+    net.set_params(p)
+    g = torch.Generator(device="cuda").manual_seed(22)
+    step = 0.01 * torch.randn(shape, device="cuda", generator=g)
+    out = net.apply(step)
+    net.check()
+    s = float(torch.sqrt(torch.mean(step.double() ** 2)))
+    rng = np.random.default_rng(23)
+    B, D, H, W = shape
+    pts = [tuple(int(rng.integers(0, n)) for n in (B, D, H, W)) for _ in range(48)]
+    pts += [(0, 0, 0, 0), (B - 1, D - 1, H - 1, W - 1), (0, D - 1, 0, W - 1)]
+    pw = p.astype(np.float64)
+    errs, mags = [], []
+    for b, z, y, x in pts:
+        lo = [max(0, c - 4) for c in (z, y, x)]
+        hi = [min(n, c + 5) for c, n in zip((z, y, x), (D, H, W))]
+        crop = to_np(step[b, lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]).astype(np.float64) / s
+        yb, _ = NL.forward(pw, crop[None], bf=True)
+        ref = yb[0, z - lo[0], y - lo[1], x - lo[2]]
+        got = float(out[b, z, y, x]) / s - crop[z - lo[0], y - lo[1], x - lo[2]]
+        errs.append(abs(got - ref))
+        mags.append(abs(ref))
+    assert max(errs) <= 8 * U * max(max(mags), 1.0), (max(errs), max(mags))
 
 
 def test_gradients_vs_oracle():
@@ -116,5 +151,6 @@ def test_deterministic_training_step():
         for _ in range(3):
             net.forward_backward(x, t)
             net.adam_step(1e-3)
+        net.check()
         outs.append(net.params())
     np.testing.assert_array_equal(outs[0], outs[1])

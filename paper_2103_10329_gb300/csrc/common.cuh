@@ -84,6 +84,7 @@ struct mgct_geom {
     std::vector<mgct::ViewGeom> h_views[8];
     // scratch owned by the handle (mgct_project / mgct_backproject)
     void *d_scratch_vol;        // one finest volume, 4 bytes per voxel
+    void *d_scratch_quads;      // projector quads of the finest grid, both ray classes (16 bytes per entry)
     double *d_scratch_part;     // reduction partials
     size_t scratch_part_count;
     int device;
@@ -217,7 +218,10 @@ __device__ __forceinline__ DF df_affine(float c, float c_lo, float a, float a_lo
 // ---------------------------------------------------------------------------
 constexpr int PJ_BX = 32;  // detector columns per block
 constexpr int PJ_BY = 8;   // detector rows per block
-constexpr int PJ_VG = 32;  // views per block group
+#ifndef MGCT_PJ_VG
+#define MGCT_PJ_VG 32
+#endif
+constexpr int PJ_VG = MGCT_PJ_VG;  // views per block group
 
 inline size_t project_blocks(int nu, int nv, int nviews) {
     if (nviews <= 0) return 0;
@@ -229,6 +233,15 @@ inline size_t project_blocks(int nu, int nv, int nviews) {
 // ---------------------------------------------------------------------------
 // Internal kernels used across translation units (host launchers)
 // ---------------------------------------------------------------------------
+// Quad copies of a volume for the projector (see Quad in project.cuh):
+// corners (jz, jb) over [-QD_PAD, n + 1] stored at corner + QD_PAD.
+constexpr int QD_PAD = 3;
+__host__ __device__ constexpr int quad_side(int n) { return n + 2 * QD_PAD - 1; }
+__host__ __device__ inline size_t quad_elems(int n) { return (size_t)quad_side(n) * n * quad_side(n); }
+// src [z][i][b] (float32, bf16 or fp16) -> quads of T (float4 for float, two
+// packed 16-bit pairs for bf16 / fp16) [z + QD_PAD][i][b + QD_PAD]
+template <typename T, typename SRC = float>
+int launch_build_quads(int n, const SRC *src, void *dst, cudaStream_t s);
 template <typename T>
 int launch_transpose_xy(int n, const T *in, T *out, cudaStream_t s);
 template <typename T>

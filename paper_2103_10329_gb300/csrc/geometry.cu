@@ -253,6 +253,7 @@ void mgct_geometry_destroy(mgct_geom *g) {
         if (g->lev[l].d_cols) cudaFree(g->lev[l].d_cols);
     }
     if (g->d_scratch_vol) cudaFree(g->d_scratch_vol);
+    if (g->d_scratch_quads) cudaFree(g->d_scratch_quads);
     if (g->d_scratch_part) cudaFree(g->d_scratch_part);
     delete g;
 }
@@ -277,6 +278,7 @@ int mgct_geometry_create(const mgct_geom_desc *d, mgct_geom **out) {
     mgct_geom *g = new mgct_geom();
     std::memset(g->lev, 0, sizeof(g->lev));
     g->d_scratch_vol = nullptr;
+    g->d_scratch_quads = nullptr;
     g->d_scratch_part = nullptr;
     g->desc = *d;
     g->desc.theta = g->desc.z = g->desc.drift = nullptr;
@@ -314,6 +316,9 @@ int mgct_geometry_create(const mgct_geom_desc *d, mgct_geom **out) {
     g->scratch_part_count = 2 * (blocks > vblocks ? blocks : vblocks) + 64;
     if (gblocks > g->scratch_part_count) g->scratch_part_count = gblocks;
     st = check_cuda(cudaMalloc(&g->d_scratch_vol, nvox * 4), "allocate scratch volume");
+    if (!st)
+        st = check_cuda(cudaMalloc(&g->d_scratch_quads, 2 * quad_elems(g->lev[0].n) * sizeof(float4)),
+                        "allocate scratch quads");
     if (!st) st = check_cuda(cudaMalloc(&g->d_scratch_part, g->scratch_part_count * sizeof(double)),
                              "allocate scratch partials");
     if (!st) st = check_cuda(cudaDeviceSynchronize(), "geometry_create");

@@ -28,13 +28,6 @@ __device__ __forceinline__ float tap(const VT *__restrict__ p, int off, bool ok)
     return ok ? to_f32(__ldg(p + off)) : 0.0f;
 }
 
-// Paired 16-bit volume (the mixed-precision solver path): entry e of a row
-// holds (V(e-1), V(e)) of the row's in-plane horizontal axis as one 32-bit
-// word, e = 0..n, with V(-1) = V(n) = 0, so both taps of a row come from one
-// aligned load.  Row length n + 1 words.
-template <typename T>
-struct Pair16 {};
-
 __device__ __forceinline__ float2 unpack2(uint32_t w, __nv_bfloat16) {
     return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
@@ -43,16 +36,32 @@ __device__ __forceinline__ float2 unpack2(uint32_t w, __half) {
     return __half22float2(h);
 }
 
+// Quad volume (the solvers' projector input): entry (jz, i, jb) holds the
+// whole bilinear footprint of a sample in plane i whose in-plane voxel
+// corner is (jz, jb) -- V(jz, jb), V(jz, jb + 1), V(jz + 1, jb),
+// V(jz + 1, jb + 1), zero outside the volume -- so one sample is one
+// unconditional 16-byte (float32) or 8-byte (16-bit) load.  Corners run over
+// [-QD_PAD, n + 1] in both in-plane axes (the clip below keeps every sample
+// of a ray inside (-2, n + 1)), stored at index corner + QD_PAD:
+// [n + 2 QD_PAD - 1][n][n + 2 QD_PAD - 1] entries.
+template <typename T>
+struct Quad {};
+
 template <typename VT>
 struct VolTraits {
     using elem = VT;
-    static constexpr bool paired = false;
+    static constexpr bool quad = false;
+};
+template <>
+struct VolTraits<Quad<float>> {
+    using elem = float4;
+    static constexpr bool quad = true;
 };
 template <typename T>
-struct VolTraits<Pair16<T>> {
-    using elem = uint32_t;
+struct VolTraits<Quad<T>> {
+    using elem = uint2;
     using half_t = T;
-    static constexpr bool paired = true;
+    static constexpr bool quad = true;
 };
 
 // Block-wide float64 sum of up to two values; result valid in thread 0.
@@ -110,6 +119,11 @@ __device__ __forceinline__ void split_coord(DF f, int &i, float &phi) {
 }
 
 constexpr int PJ_CHUNK = 16;  // planes stepped in float32 from one double-float anchor
+#ifndef MGCT_PJ_UNROLL
+#define MGCT_PJ_UNROLL 1
+#endif
+#define MGCT_PRAGMA_S(x) _Pragma(#x)
+#define MGCT_PRAGMA(x) MGCT_PRAGMA_S(x)
 
 // Line integral of one ray; returns A vol for pixel (ju, jv) of view G.
 // The ray's crossing with the central plane and its slopes are set up in
@@ -147,8 +161,15 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
     float lo = 0.0f, hi = (float)(n - 1);
     clip_planes(pb.hi, rb.hi, ic, (float)n, lo, hi);
     clip_planes(pz.hi, rz.hi, ic, (float)n, lo, hi);
-    const int i0 = max(0, (int)floorf(lo) - 1);
-    const int i1 = min(n - 1, (int)ceilf(hi) + 1);
+    // Planes outside [floor(lo), ceil(hi)] lie beyond a boundary by at least
+    // |r| (1 - rounding) and sample zero; within it both coordinates stay in
+    // (-1 - |r|, n + |r|) with |r| <= 1 (x or y is the major axis and z never
+    // is), i.e. in (-2, n + 1).
+    if (!(lo <= hi)) return RaySum{0.0f, dl_h * a.h};
+    const int i0 = max(0, (int)floorf(lo));
+    const int i1 = min(n - 1, (int)ceilf(hi));
+    const unsigned qmax = (unsigned)quad_elems(n) - 1u;
+    (void)qmax;
     float acc = 0.0f;
     for (int c0 = i0; c0 <= i1; c0 += PJ_CHUNK) {
         const float d0 = __fsub_rn((float)c0, ic);  // exact
@@ -158,6 +179,7 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
         split_coord(df_add(df_add(pz, df_mul_f(rz, d0)), DF{ic, 0.0f}), Iz, phiz);
         const int cnt = min(PJ_CHUNK, i1 - c0 + 1);
         float part = 0.0f;
+        MGCT_PRAGMA(unroll MGCT_PJ_UNROLL)
         for (int k = 0; k < cnt; ++k) {
             const int i = c0 + k;
             const float gb = fmaf((float)k, rb.hi, phib);
@@ -167,19 +189,24 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
             const int jb = Ib + (int)fb0, jz = Iz + (int)fz0;
             const bool z0 = (unsigned)jz < (unsigned)n, z1 = (unsigned)(jz + 1) < (unsigned)n;
             float v00, v10, v01, v11;
-            if constexpr (VolTraits<VT>::paired) {
-                // one word per row: entry jb + 1 = (V(jb), V(jb + 1))
-                const bool bok = (unsigned)(jb + 1) <= (unsigned)n;
-                const int row0 = (jz * n + i) * (n + 1) + jb + 1;
-                const int row1 = row0 + n * (n + 1);
-                const uint32_t w0 = (bok && z0) ? __ldg(base + row0) : 0u;
-                const uint32_t w1 = (bok && z1) ? __ldg(base + row1) : 0u;
-                const float2 p0 = unpack2(w0, typename VolTraits<VT>::half_t());
-                const float2 p1 = unpack2(w1, typename VolTraits<VT>::half_t());
-                v00 = p0.x;
-                v10 = p0.y;
-                v01 = p1.x;
-                v11 = p1.y;
+            if constexpr (VolTraits<VT>::quad) {
+                // the clip keeps q in range; the unsigned min only guarantees it
+                const unsigned q = min((unsigned)(((jz + QD_PAD) * n + i) * quad_side(n) + jb + QD_PAD), qmax);
+                if constexpr (std::is_same<E, float4>::value) {
+                    const float4 Q = __ldg(base + q);
+                    v00 = Q.x;
+                    v10 = Q.y;
+                    v01 = Q.z;
+                    v11 = Q.w;
+                } else {
+                    const uint2 Q = __ldg(base + q);
+                    const float2 p0 = unpack2(Q.x, typename VolTraits<VT>::half_t());
+                    const float2 p1 = unpack2(Q.y, typename VolTraits<VT>::half_t());
+                    v00 = p0.x;
+                    v10 = p0.y;
+                    v01 = p1.x;
+                    v11 = p1.y;
+                }
             } else {
                 const bool b0 = (unsigned)jb < (unsigned)n, b1 = (unsigned)(jb + 1) < (unsigned)n;
                 const int row0 = (jz * n + i) * n + jb;  // may be out of range; loads are predicated
@@ -208,8 +235,11 @@ __device__ __forceinline__ RaySum ray_integral(const ViewGeom &G, const ProjArgs
 // group, column tile): the blocks resident at any time share that band and
 // its rows stay in L2.
 
+#ifndef MGCT_PJ_MINB
+#define MGCT_PJ_MINB 8  // 32 registers: 64 resident warps hide the gather latency
+#endif
 template <typename VT, typename Epi>
-__global__ void __launch_bounds__(PJ_BX *PJ_BY)
+__global__ void __launch_bounds__(PJ_BX *PJ_BY, MGCT_PJ_MINB)
     k_project(ProjArgs a, const typename VolTraits<VT>::elem *__restrict__ vol,
               const typename VolTraits<VT>::elem *__restrict__ volT, Epi epi) {
     __shared__ ViewGeom G;

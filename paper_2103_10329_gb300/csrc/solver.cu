@@ -26,9 +26,6 @@ int launch_scaled_copy(size_t count, const float *d, const double *alpha, float 
 int launch_update_choice(size_t count, float *mu, const float *d, const float *dl, const double *st, float lam,
                          cudaStream_t s);
 int launch_axpy(size_t count, float a, const float *x, float *y, cudaStream_t s);
-template <typename T>
-int launch_cast_pairs(int n, const float *in, uint32_t *py, uint32_t *px, cudaStream_t s);
-
 int launch_column_table(const mgct_geom *g, int level, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
     const int K = g->desc.n_views;
@@ -63,7 +60,7 @@ static size_t proj_blocks(const mgct_geom *g, const LevelInfo &L) {
 
 struct LWSpace {
     float *r, *grad, *d, *muT;
-    uint32_t *pairs;              // paired 16-bit projector input, two layouts of n^2 (n+1) words
+    float4 *quads;                // projector input: quad copies for y-major then x-major rays
     double *part, *sums, *stats;  // sums: [0] r2, [1] <r,Ad>, [2] |Ad|^2 ; stats: 4
 };
 
@@ -74,7 +71,7 @@ static LWSpace carve_lw(const mgct_geom *g, int level, Carver &c) {
     w.grad = c.take<float>(vox(L));
     w.d = c.take<float>(vox(L));
     w.muT = c.take<float>(vox(L));
-    w.pairs = c.take<uint32_t>(2 * (size_t)L.n * L.n * (L.n + 1));
+    w.quads = c.take<float4>(2 * quad_elems(L.n));  // sized for float32 quads (16-bit ones use half)
     w.part = c.take<double>(2 * proj_blocks(g, L) + 64);
     w.sums = c.take<double>(8);
     w.stats = c.take<double>(8);
@@ -148,6 +145,22 @@ static int check_ws(const mgct_geom *g, int op, int level, const void *ws, size_
 // ---------------------------------------------------------------------------
 // Solver steps
 // ---------------------------------------------------------------------------
+// A v over every view through quad copies of v in storage type ST: the
+// transpose of v into `vT` (float32 scratch), the quads of both ray classes
+// into `quads`, then the projector with epilogue `e`.
+template <typename ST, typename Epi>
+static int project_quads(const mgct_geom *g, int level, const float *v, float *vT, float4 *quads, const Epi &e,
+                         cudaStream_t s, int *nb) {
+    using QE = typename VolTraits<Quad<ST>>::elem;
+    const LevelInfo &L = g->lev[level];
+    QE *qy = reinterpret_cast<QE *>(quads);
+    QE *qx = qy + quad_elems(L.n);
+    MGCT_TRY(launch_transpose_xy<float>(L.n, v, vT, s));
+    MGCT_TRY(launch_build_quads<ST>(L.n, v, qy, s));
+    MGCT_TRY(launch_build_quads<ST>(L.n, vT, qx, s));
+    return launch_project<Quad<ST>>(g, level, 0, g->desc.n_views, 1, qy, qx, e, s, nb);
+}
+
 // ST: storage type of the copies the projector and back-projector read (the
 // shadow of mu, the residual sinogram, the shadow of the search direction).
 //
@@ -164,15 +177,8 @@ static int lw_direction(const mgct_geom *g, int level, const float *mu, const fl
     ST *r = reinterpret_cast<ST *>(w.r);
     int nb = 0;
     EpiResidual<ST, true> er{r, b, w.part, L.nu, L.nv, K};
-    if constexpr (F32) {
-        MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
-        MGCT_TRY(launch_project<float>(g, level, 0, K, 1, mu, w.muT, er, s, &nb));
-    } else {
-        // paired 16-bit shadows of mu: two taps per load
-        const size_t half = (size_t)L.n * L.n * (L.n + 1);
-        MGCT_TRY(launch_cast_pairs<ST>(L.n, mu, w.pairs, w.pairs + half, s));
-        MGCT_TRY(launch_project<Pair16<ST>>(g, level, 0, K, 1, w.pairs, w.pairs + half, er, s, &nb));
-    }
+    (void)F32;
+    MGCT_TRY(project_quads<ST>(g, level, mu, w.muT, w.quads, er, s, &nb));
     (void)nv3;
     MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
     MGCT_TRY(launch_backproject<1, ST, true>(g, level, 0, K, 1, r, w.grad, 0, s));
@@ -194,16 +200,8 @@ static int lw_line_search(const mgct_geom *g, int level, const float *dir, float
     const size_t nv3 = vox(L);
     int nb = 0;
     EpiDualDot<ST> ed{reinterpret_cast<ST *>(w.r), w.part, L.nu, L.nv, K};
-    if constexpr (std::is_same<ST, float>::value) {
-        MGCT_TRY(launch_transpose_xy<float>(L.n, dir, spare, s));
-        MGCT_TRY(launch_project<float>(g, level, 0, K, 1, dir, spare, ed, s, &nb));
-    } else {
-        const size_t half = (size_t)L.n * L.n * (L.n + 1);
-        MGCT_TRY(launch_cast_pairs<ST>(L.n, dir, w.pairs, w.pairs + half, s));
-        MGCT_TRY(launch_project<Pair16<ST>>(g, level, 0, K, 1, w.pairs, w.pairs + half, ed, s, &nb));
-    }
+    MGCT_TRY(project_quads<ST>(g, level, dir, spare, w.quads, ed, s, &nb));
     (void)nv3;
-    (void)spare;
     return launch_sum_partials(w.part, nb, 2, w.sums + slot, s);
 }
 
@@ -353,18 +351,24 @@ int mgct_project(const mgct_geom *g, int level, int view0, int nviews, int strid
     }
     int nb = 0;
     double *part = sumsq ? g->d_scratch_part : nullptr;
+    // the volume's quads (in its own precision) for both ray classes
     auto run = [&](auto vtag, auto otag) -> int {
         using VT = decltype(vtag);
         using OT = decltype(otag);
+        using QE = typename VolTraits<Quad<VT>>::elem;
         const VT *v = static_cast<const VT *>(vol);
         VT *vT = static_cast<VT *>(g->d_scratch_vol);
+        QE *qy = static_cast<QE *>(g->d_scratch_quads);
+        QE *qx = qy + quad_elems(L.n);
         MGCT_TRY(launch_transpose_xy<VT>(L.n, v, vT, s));
+        MGCT_TRY((launch_build_quads<VT, VT>(L.n, v, qy, s)));
+        MGCT_TRY((launch_build_quads<VT, VT>(L.n, vT, qx, s)));
         if (b) {
             EpiResidual<OT> e{static_cast<OT *>(out), b, part, L.nu, L.nv, nviews};
-            return launch_project<VT>(g, level, view0, nviews, stride, v, vT, e, s, &nb);
+            return launch_project<Quad<VT>>(g, level, view0, nviews, stride, qy, qx, e, s, &nb);
         }
         EpiStore<OT> e{static_cast<OT *>(out), L.nu, L.nv};
-        return launch_project<VT>(g, level, view0, nviews, stride, v, vT, e, s, &nb);
+        return launch_project<Quad<VT>>(g, level, view0, nviews, stride, qy, qx, e, s, &nb);
     };
     auto run_v = [&](auto vtag) -> int {
         switch (ot) {

@@ -2,6 +2,8 @@
 // restriction and prolongation (Alg. 1), the Landweber update with soft
 // thresholding, and deterministic float64 reductions.  All are bound by HBM
 // bandwidth; each reads and writes its arrays once with coalesced accesses.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace mgct {
@@ -71,13 +73,7 @@ int launch_cast_transpose(int n, const float *in, T *out, T *outT, cudaStream_t 
 template int launch_cast_transpose<__nv_bfloat16>(int, const float *, __nv_bfloat16 *, __nv_bfloat16 *, cudaStream_t);
 template int launch_cast_transpose<__half>(int, const float *, __half *, __half *, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// float32 vol [z][y][x] -> paired 16-bit rows for the projector:
-//   Py[z][y][e] = (V[z][y][e-1], V[z][y][e])   (y-major rays, pairs along x)
-//   Px[z][x][e] = (V[z][e-1][x], V[z][e][x])   (x-major rays, pairs along y)
-// e = 0..n, zero outside [0, n-1]; rows of n + 1 words.  One pass through a
-// 34 x 34 shared tile (the 32 x 32 block plus a one-voxel halo).
-// ---------------------------------------------------------------------------
+// two float32 values rounded to 16 bits, packed low then high
 __device__ __forceinline__ uint32_t pack2(float lo, float hi, __nv_bfloat16) {
     const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
     const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
@@ -89,47 +85,45 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi, __half) {
     return a | (b << 16);
 }
 
+// ---------------------------------------------------------------------------
+// Quad copies: dst[zq][i][bq] = (V(jz, jb), V(jz, jb + 1), V(jz + 1, jb),
+// V(jz + 1, jb + 1)) of plane i, jz = zq - QD_PAD, jb = bq - QD_PAD, zero
+// outside the volume.  Reads coalesced along b (each value four times, from
+// cache); one 16- or 8-byte store per entry.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 make_quad(float a, float b, float c, float d, float) { return make_float4(a, b, c, d); }
 template <typename T>
-__global__ void __launch_bounds__(256) k_cast_pairs(int n, const float *__restrict__ in, uint32_t *__restrict__ py,
-                                                    uint32_t *__restrict__ px) {
-    __shared__ float tile[34][35];  // [y - y0 + 1][x - x0 + 1]
-    const int z = blockIdx.z;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    const size_t slab = (size_t)z * n * n;
-    for (int t = threadIdx.x + 32 * threadIdx.y; t < 34 * 34; t += 256) {
-        const int ty = t / 34, tx = t % 34;
-        const int y = y0 + ty - 1, x = x0 + tx - 1;
-        tile[ty][tx] = (x >= 0 && x < n && y >= 0 && y < n) ? in[slab + (size_t)y * n + x] : 0.0f;
-    }
-    __syncthreads();
-    const size_t prow = (size_t)(n + 1);
-    // entries e = x0 .. x0 + 31 of rows y (plus e = n in the last column block)
-    for (int dy = threadIdx.y; dy < 32; dy += 8) {
-        const int y = y0 + dy;
-        if (y >= n) break;
-        const int e = x0 + threadIdx.x;
-        if (e <= n) py[(slab / n + y) * prow + e] = pack2(tile[dy + 1][threadIdx.x], tile[dy + 1][threadIdx.x + 1], T());
-        if (threadIdx.x == 31 && e + 1 == n)
-            py[(slab / n + y) * prow + n] = pack2(tile[dy + 1][32], 0.0f, T());
-    }
-    for (int dx = threadIdx.y; dx < 32; dx += 8) {
-        const int x = x0 + dx;
-        if (x >= n) break;
-        const int e = y0 + threadIdx.x;
-        if (e <= n) px[((size_t)z * n + x) * prow + e] = pack2(tile[threadIdx.x][dx + 1], tile[threadIdx.x + 1][dx + 1], T());
-        if (threadIdx.x == 31 && e + 1 == n)
-            px[((size_t)z * n + x) * prow + n] = pack2(tile[32][dx + 1], 0.0f, T());
-    }
+__device__ __forceinline__ uint2 make_quad(float a, float b, float c, float d, T) {
+    return make_uint2(pack2(a, b, T()), pack2(c, d, T()));
 }
 
-template <typename T>
-int launch_cast_pairs(int n, const float *in, uint32_t *py, uint32_t *px, cudaStream_t s) {
-    dim3 grid((n + 31) / 32, (n + 31) / 32, n);
-    MGCT_KERNEL(KK_TRANSPOSE, s, k_cast_pairs<T><<<grid, dim3(32, 8), 0, s>>>(n, in, py, px));
+template <typename T, typename QE, typename SRC>
+__global__ void __launch_bounds__(128) k_build_quads(int n, const SRC *__restrict__ src, QE *__restrict__ dst) {
+    const int side = quad_side(n);
+    const int bq = blockIdx.x * 128 + threadIdx.x;
+    if (bq >= side) return;
+    const int i = blockIdx.y, zq = blockIdx.z;
+    const int jz = zq - QD_PAD, jb = bq - QD_PAD;
+    auto V = [&](int z, int b) -> float {
+        return ((unsigned)z < (unsigned)n && (unsigned)b < (unsigned)n) ? to_f32(__ldg(src + ((size_t)z * n + i) * n + b))
+                                                                       : 0.0f;
+    };
+    dst[((size_t)zq * n + i) * side + bq] = make_quad(V(jz, jb), V(jz, jb + 1), V(jz + 1, jb), V(jz + 1, jb + 1), T());
+}
+
+template <typename T, typename SRC>
+int launch_build_quads(int n, const SRC *src, void *dst, cudaStream_t s) {
+    using QE = typename std::conditional<std::is_same<T, float>::value, float4, uint2>::type;
+    dim3 grid((quad_side(n) + 127) / 128, n, quad_side(n));
+    MGCT_KERNEL(KK_TRANSPOSE, s, k_build_quads<T, QE, SRC><<<grid, 128, 0, s>>>(n, src, static_cast<QE *>(dst)));
     return MGCT_OK;
 }
-template int launch_cast_pairs<__nv_bfloat16>(int, const float *, uint32_t *, uint32_t *, cudaStream_t);
-template int launch_cast_pairs<__half>(int, const float *, uint32_t *, uint32_t *, cudaStream_t);
+template int launch_build_quads<float, float>(int, const float *, void *, cudaStream_t);
+template int launch_build_quads<__nv_bfloat16, float>(int, const float *, void *, cudaStream_t);
+template int launch_build_quads<__half, float>(int, const float *, void *, cudaStream_t);
+template int launch_build_quads<__nv_bfloat16, __nv_bfloat16>(int, const __nv_bfloat16 *, void *, cudaStream_t);
+template int launch_build_quads<__half, __half>(int, const __half *, void *, cudaStream_t);
+
 
 // ---------------------------------------------------------------------------
 // Eq. 5 stencil: out = p * in, zero padding.  Block = 32 x 8 columns; each

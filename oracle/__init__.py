@@ -460,22 +460,35 @@ def data_levels(b: np.ndarray, levels: int):
 
 def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
               lam: float = 0.0, n_subsets: int = 8, alpha: float | None = None,
-              precond: bool = True, stats: list | None = None) -> np.ndarray:
+              precond: bool = True, stats: list | None = None, fas: bool = False,
+              b: np.ndarray | None = None) -> np.ndarray:
     """Alg. 1 on grid `level`; returns the updated estimate on that grid.
-    parity unpinned beyond L = 1 (no closed form); checked against the paper's
-    qualitative claim and against the GPU."""
+
+    The coarse problem's data is the restricted radiographs R b (Alg. 1).
+    With fas=True it is instead the full-approximation-scheme data
+        b_c = R (b_g - P_g mu) + P_c (R mu),
+    b_g being this grid's own data (`b`, else b_levels[level]): a variant
+    that is not in the paper (Brandt's FAS coarse equation), under which an
+    exact solution of the fine problem is a fixed point of the iteration.
+    parity unpinned beyond L = 1 for the plain recursion (no closed form):
+    checked against the paper's qualitative claim and against the GPU; the FAS
+    form is pinned by its fixed point."""
     g = level_geometry(scan, level)
     mu = np.asarray(mu, dtype=np.float64)
+    b_here = b_levels[level] if b is None else np.asarray(b, dtype=np.float64)
     if level + 1 < levels:
         mu_c = restrict_volume(mu)
+        if fas:
+            b_c = restrict_sino(b_here - project(g, mu)) + project(level_geometry(scan, level + 1), mu_c)
+        else:
+            b_c = b_levels[level + 1]
         if level + 1 < levels - 1:
             mu_c_new = multigrid(scan, mu_c, b_levels, levels, level + 1, lam, n_subsets,
-                                 alpha, precond, stats)
+                                 alpha, precond, stats, fas=fas, b=b_c)
         else:
-            mu_c_new = osemtr_pass(level_geometry(scan, level + 1), mu_c, b_levels[level + 1],
-                                   n_subsets)
+            mu_c_new = osemtr_pass(level_geometry(scan, level + 1), mu_c, b_c, n_subsets)
         mu = mu + prolong(mu_c_new - mu_c)
-    mu, st = landweber_step(g, mu, b_levels[level], alpha=alpha, lam=lam, precond=precond,
+    mu, st = landweber_step(g, mu, b_here, alpha=alpha, lam=lam, precond=precond,
                             slice_axis=scan.slice_axis)
     if stats is not None:
         st["level"] = level
@@ -484,12 +497,14 @@ def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
 
 
 def reconstruct(scan: Scan, b: np.ndarray, iters: int = 2, levels: int = 2, lam: float = 0.0,
-                n_subsets: int = 8, mu0: np.ndarray | None = None, stats: list | None = None):
-    """`iters` multigrid iterations at grid 0 from mu = 0 (Fig. 3: one or two)."""
+                n_subsets: int = 8, mu0: np.ndarray | None = None, stats: list | None = None,
+                fas: bool = False):
+    """`iters` multigrid iterations at grid 0 from mu = 0 (Fig. 3: one or two);
+    fas=True takes the FAS coarse data (see multigrid)."""
     bl = data_levels(b, levels)
     mu = np.zeros((scan.n,) * 3) if mu0 is None else np.asarray(mu0, dtype=np.float64)
     for _ in range(iters):
-        mu = multigrid(scan, mu, bl, levels, 0, lam, n_subsets, stats=stats)
+        mu = multigrid(scan, mu, bl, levels, 0, lam, n_subsets, stats=stats, fas=fas)
     return mu
 
 

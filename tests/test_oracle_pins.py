@@ -422,6 +422,55 @@ def test_multigrid_structure_two_levels():
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
 
 
+def _fas_case(n=16, nviews=40, levels=2):
+    scan = make_scan(n, nviews=nviews, seed=21)
+    ph = synth.ellipsoids(6, 3, axis_lo=0.08, axis_hi=0.3)
+    x = synth.voxelize_ellipsoids(ph, n, supersample=1).numpy().astype(np.float64)
+    b = O.project(O.level_geometry(scan, 0), x)
+    return scan, x, O.data_levels(b, levels)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_multigrid_fas_exact_solution_is_fixed_point(levels):
+    """With consistent data b = P x and mu = x, the FAS coarse data is
+    R (b - P x) + P_c R x = P_c R x, which the coarse solver leaves at R x,
+    and the fine residual is zero: x is a fixed point.  The plain recursion
+    (coarse data R b != P_c R x) moves away from it -- the plateau that FAS
+    removes."""
+    scan, x, bl = _fas_case(levels=levels)
+    fas = O.multigrid(scan, x, bl, levels, fas=True)
+    plain = O.multigrid(scan, x, bl, levels, fas=False)
+    assert np.abs(fas - x).max() <= 1e-12 * np.abs(x).max()
+    assert np.abs(plain - x).max() >= 1e-2 * np.abs(x).max()
+
+
+def test_multigrid_fas_first_iteration_from_zero_is_plain():
+    """From mu = 0 the FAS coarse data R (b - P 0) + P_c 0 is R b: the first
+    iteration is the plain one."""
+    scan, x, bl = _fas_case(n=8, nviews=12)
+    mu0 = np.zeros_like(x)
+    np.testing.assert_allclose(O.multigrid(scan, mu0, bl, 2, fas=True), O.multigrid(scan, mu0, bl, 2),
+                               rtol=0, atol=1e-14)
+
+
+def test_multigrid_fas_converges_past_the_plain_plateau():
+    """On consistent data the plain recursion stalls (its fixed point is not
+    the solution) while FAS keeps converging: after 24 iterations its error is
+    below half the plain one and still falling."""
+    scan, x, bl = _fas_case()
+    rng = float(x.max() - x.min())
+    err = {}
+    for fas in (False, True):
+        mu = np.zeros_like(x)
+        e = []
+        for _ in range(24):
+            mu = O.multigrid(scan, mu, bl, 2, fas=fas)
+            e.append(np.sqrt(np.mean((mu - x) ** 2)) / rng)
+        err[fas] = e
+    assert err[True][-1] < 0.5 * err[False][-1], (err[True][-1], err[False][-1])
+    assert all(a > b for a, b in zip(err[True][-6:], err[True][-5:]))
+
+
 @pytest.mark.slow
 def test_pmgl_beats_sirt_at_equal_cost():
     """Sec. 3 / Fig. 4: after 2 iterations preconditioned multigrid Landweber is

@@ -186,7 +186,12 @@ typedef struct {
                              of the search direction and a 16-bit residual sinogram; mu itself
                              (the master copy), b, the filter and the update stay float32,
                              accumulation is float32, alpha and the norms float64 */
-    int32_t reserved0;    /* must be 0 */
+    int32_t coarse_fas;   /* multigrid only.  0: the coarse problem's data is the restricted
+                             radiographs R b (Alg. 1).  1: the full-approximation-scheme data
+                             R (b_g - A_g mu) + A_c (R mu), rebuilt each iteration (one extra A
+                             on every grid but the coarsest; not in the paper): the fine
+                             solution becomes a fixed point, removing the plateau of the
+                             plain recursion on consistent data */
     const float *learned_corr; /* reserved, must be NULL */
 } mgct_lw_opts;
 
@@ -235,9 +240,11 @@ int mgct_multigrid_iteration(const mgct_geom *geom, float *vol, const float *b, 
 /* Alg. 1 without the grid-0 Landweber step: restrict mu, recurse (or one
  * OS-EMTR pass on the coarsest grid) and add the prolongated coarse change.
  * mgct_multigrid_iteration = mgct_multigrid_coarse + mgct_landweber_step at
- * grid 0.  Same arguments as mgct_multigrid_iteration without b. */
-int mgct_multigrid_coarse(const mgct_geom *geom, float *vol, void *workspace, size_t ws_bytes,
-                          const mgct_lw_opts *opts, mgct_lw_stats *stats, mgct_stream stream);
+ * grid 0.  Same arguments as mgct_multigrid_iteration; b (the grid-0 data)
+ * may be NULL unless opts->coarse_fas. */
+int mgct_multigrid_coarse(const mgct_geom *geom, float *vol, const float *b, void *workspace,
+                          size_t ws_bytes, const mgct_lw_opts *opts, mgct_lw_stats *stats,
+                          mgct_stream stream);
 
 /* The step alpha d of one Landweber step (Eq. 4: d = p * A^T (b - A mu),
  * alpha from the line search or fixed) into step (float32 [n_g]^3), without

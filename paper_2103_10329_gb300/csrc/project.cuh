@@ -269,6 +269,19 @@ struct EpiStore {
     }
 };
 
+// out = b + A vol (out may alias b: each ray reads its own entry first)
+struct EpiPlus {
+    float *out;
+    const float *b;
+    int nu, nv;
+    __device__ void operator()(int i, int, int jv, int ju, bool active, float acc, float dlh) const {
+        if (active) {
+            const size_t idx = ((size_t)i * nv + jv) * nu + ju;
+            out[idx] = b[idx] + acc * dlh;
+        }
+    }
+};
+
 // r = b - A vol and the block's sum of r^2 (float64) into part[block].
 // WEIGHTED = false: out = r.  WEIGHTED = true: out = r * dlh (the ray's path
 // length per plane), which the back-projector then need not recompute.

@@ -96,6 +96,7 @@ static EMSpace carve_em(const mgct_geom *g, int level, Carver &c) {
 
 struct MGSpace {
     float *b[8], *mu[8], *old[8];
+    float *bf[8];  // FAS coarse data per grid (grids 1 .. L-1)
     float *pi;
     int prepared_flag;
     void *lw_base, *em_base;
@@ -107,6 +108,7 @@ static MGSpace carve_mg(const mgct_geom *g, Carver &c) {
     std::memset(&m, 0, sizeof(m));
     for (int l = 1; l < g->levels; ++l) {
         m.b[l] = c.take<float>(sino_elems(g, g->lev[l]));
+        m.bf[l] = c.take<float>(sino_elems(g, g->lev[l]));
         m.mu[l] = c.take<float>(vox(g->lev[l]));
         m.old[l] = c.take<float>(vox(g->lev[l]));
     }
@@ -293,25 +295,47 @@ static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *
     return MGCT_OK;
 }
 
-static int multigrid_level(const mgct_geom *g, int level, float *mu, const MGSpace &m, const float *b0,
+// Alg. 1 on grid `level` with this grid's data `b`: restrict mu, recurse (or
+// one OS-EMTR pass on the coarsest grid), add the prolongated coarse change,
+// then one Landweber step (unless skip_landweber).  The coarse data is R b,
+// prepared once (m.b), or with o.coarse_fas the full-approximation-scheme
+// data R (b - A mu) + A_c (R mu), built here every call (m.bf): a variant
+// outside the paper under which the fine solution is a fixed point.
+static int multigrid_level(const mgct_geom *g, int level, float *mu, const MGSpace &m, const float *b,
                            const mgct_lw_opts &o, mgct_lw_stats *stats, cudaStream_t s, bool skip_landweber = false) {
     const int Lc = g->levels;
     trace_tag(level);
     if (level + 1 < Lc) {
-        const int nf = g->lev[level].n;
+        const LevelInfo &F = g->lev[level], &C = g->lev[level + 1];
+        const int K = g->desc.n_views;
         float *mc = m.mu[level + 1], *oc = m.old[level + 1];
-        MGCT_TRY(launch_restrict_volume(nf, mu, mc, s));
-        MGCT_TRY(launch_copy(vox(g->lev[level + 1]), mc, oc, s));
+        MGCT_TRY(launch_restrict_volume(F.n, mu, mc, s));
+        MGCT_TRY(launch_copy(vox(C), mc, oc, s));
+        const float *bc = m.b[level + 1];
+        if (o.coarse_fas) {
+            // the Landweber workspace's residual, transpose and quads serve as scratch
+            Carver cw(m.lw_base);
+            LWSpace w = carve_lw(g, 0, cw);
+            int nb = 0;
+            EpiResidual<float, false> er{w.r, b, nullptr, F.nu, F.nv, K};
+            MGCT_TRY(project_quads<float>(g, level, mu, w.muT, w.quads, er, s, &nb));
+            MGCT_TRY(launch_restrict_sino(K, F.nv, F.nu, w.r, m.bf[level + 1], s));
+            trace_tag(level + 1);
+            EpiPlus ep{m.bf[level + 1], m.bf[level + 1], C.nu, C.nv};
+            MGCT_TRY(project_quads<float>(g, level + 1, mc, w.muT, w.quads, ep, s, &nb));
+            trace_tag(level);
+            bc = m.bf[level + 1];
+        }
         if (level + 1 < Lc - 1) {
-            MGCT_TRY(multigrid_level(g, level + 1, mc, m, b0, o, stats, s));
+            MGCT_TRY(multigrid_level(g, level + 1, mc, m, bc, o, stats, s));
         } else {
             int M = o.n_subsets > 0 ? o.n_subsets : 8;
-            MGCT_TRY(osemtr(g, level + 1, M, mc, m.b[level + 1], m.pi, m.em_base, s));
+            MGCT_TRY(osemtr(g, level + 1, M, mc, bc, m.pi, m.em_base, s));
         }
-        MGCT_TRY(launch_prolong_add(g->lev[level + 1].n, mc, oc, mu, s));
+        trace_tag(level);
+        MGCT_TRY(launch_prolong_add(C.n, mc, oc, mu, s));
     }
     if (skip_landweber) return MGCT_OK;
-    const float *b = level == 0 ? b0 : m.b[level];
     return landweber(g, level, mu, b, m.lw_base, o, stats ? stats + level : nullptr, s);
 }
 
@@ -320,8 +344,9 @@ static int check_opts(const mgct_lw_opts *o) {
     if (o->learned_corr) return set_error(MGCT_EINVAL, "learned_corr is reserved and must be NULL");
     if (!(o->lambda >= 0.0)) return set_error(MGCT_EINVAL, "lambda must be >= 0");
     if (o->n_subsets < 0) return set_error(MGCT_EINVAL, "n_subsets must be >= 0");
-    if (o->storage < MGCT_F32 || o->storage > MGCT_F16 || o->reserved0 != 0)
-        return set_error(MGCT_EINVAL, "storage must be MGCT_F32, MGCT_BF16 or MGCT_F16 (reserved0 = 0)");
+    if (o->storage < MGCT_F32 || o->storage > MGCT_F16)
+        return set_error(MGCT_EINVAL, "storage must be MGCT_F32, MGCT_BF16 or MGCT_F16");
+    if (o->coarse_fas != 0 && o->coarse_fas != 1) return set_error(MGCT_EINVAL, "coarse_fas must be 0 or 1");
     return MGCT_OK;
 }
 
@@ -509,16 +534,17 @@ int mgct_multigrid_iteration(const mgct_geom *g, float *vol, const float *b, voi
     return multigrid_level(g, 0, vol, m, b, *o, stats, reinterpret_cast<cudaStream_t>(stream));
 }
 
-int mgct_multigrid_coarse(const mgct_geom *g, float *vol, void *ws, size_t bytes, const mgct_lw_opts *o,
-                          mgct_lw_stats *stats, mgct_stream stream) {
+int mgct_multigrid_coarse(const mgct_geom *g, float *vol, const float *b, void *ws, size_t bytes,
+                          const mgct_lw_opts *o, mgct_lw_stats *stats, mgct_stream stream) {
     if (!g) return set_error(MGCT_EINVAL, "geometry handle is NULL");
     MGCT_TRY(check_opts(o));
     MGCT_TRY(check_ptr(vol, "vol"));
+    MGCT_TRY(check_ptr(b, "b", !o->coarse_fas));
     MGCT_TRY(check_ptr(stats, "stats", true));
     MGCT_TRY(check_ws(g, MGCT_WS_MULTIGRID, 0, ws, bytes));
     Carver c(ws);
     MGSpace m = carve_mg(g, c);
-    return multigrid_level(g, 0, vol, m, nullptr, *o, stats, reinterpret_cast<cudaStream_t>(stream), true);
+    return multigrid_level(g, 0, vol, m, b, *o, stats, reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 int mgct_landweber_direction(const mgct_geom *g, int level, const float *vol, const float *b, void *ws, size_t bytes,

@@ -36,7 +36,7 @@ class GeomDesc(ctypes.Structure):
 class LwOpts(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("precondition", ctypes.c_int32), ("n_subsets", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("coarse_fas", ctypes.c_int32),
                 ("learned_corr", ctypes.c_void_p)]
 
 
@@ -77,7 +77,7 @@ def lib():
     L.mgct_trace_enable.argtypes = [i]
     L.mgct_trace_read.argtypes = [vp, vp, i]
     L.mgct_trace_read_level.argtypes = [i, vp, vp, i]
-    L.mgct_multigrid_coarse.argtypes = [vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp]
+    L.mgct_multigrid_coarse.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp]
     L.mgct_landweber_direction.argtypes = [vp, i, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp, vp]
     L.mgct_landweber_learned.argtypes = [vp, i, vp, vp, vp, sz, ctypes.POINTER(LwOpts), vp, vp, sz, vp, vp]
     L.mgct_axpy.argtypes = [sz, ctypes.c_float, vp, vp, vp]
@@ -286,9 +286,9 @@ def workspace(geom: Geometry, op: int, level: int = 0, device="cuda") -> torch.T
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
-def _opts(alpha, lam, precond, n_subsets, storage=torch.float32):
+def _opts(alpha, lam, precond, n_subsets, storage=torch.float32, fas=False):
     return LwOpts(float(alpha) if alpha is not None else 0.0, float(lam), 1 if precond else 0,
-                  int(n_subsets), _DT[storage], 0, None)
+                  int(n_subsets), _DT[storage], 1 if fas else 0, None)
 
 
 def landweber_step(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, level: int = 0, alpha=None,
@@ -323,8 +323,10 @@ def multigrid_prepare(geom: Geometry, b: torch.Tensor, ws: torch.Tensor):
 
 def multigrid_iteration(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, ws: torch.Tensor, alpha=None,
                         lam: float = 0.0, precond: bool = True, n_subsets: int = 8,
-                        stats: torch.Tensor | None = None, storage=torch.float32):
-    o = _opts(alpha, lam, precond, n_subsets, storage)
+                        stats: torch.Tensor | None = None, storage=torch.float32, fas: bool = False):
+    """One Alg. 1 iteration at grid 0; fas=True takes the full-approximation-
+    scheme coarse data R(b - A mu) + A_c(R mu) (a variant outside the paper)."""
+    o = _opts(alpha, lam, precond, n_subsets, storage, fas)
     _check(lib().mgct_multigrid_iteration(geom.handle, _ptr(vol, "vol", torch.float32),
                                           _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(),
                                           ctypes.byref(o), _ptr(stats, "stats", torch.float64), _stream()))
@@ -332,10 +334,14 @@ def multigrid_iteration(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, ws: 
 
 
 def multigrid_coarse(geom: Geometry, vol: torch.Tensor, ws: torch.Tensor, n_subsets: int = 8,
-                     stats: torch.Tensor | None = None, storage=torch.float32, lam: float = 0.0):
-    o = _opts(None, lam, True, n_subsets, storage)
-    _check(lib().mgct_multigrid_coarse(geom.handle, _ptr(vol, "vol", torch.float32), _ptr(ws, "ws"), ws.numel(),
-                                       ctypes.byref(o), _ptr(stats, "stats", torch.float64), _stream()))
+                     stats: torch.Tensor | None = None, storage=torch.float32, lam: float = 0.0,
+                     b: torch.Tensor | None = None, fas: bool = False):
+    """Alg. 1 without the grid-0 Landweber step; b (grid-0 data) is needed
+    with fas=True."""
+    o = _opts(None, lam, True, n_subsets, storage, fas)
+    _check(lib().mgct_multigrid_coarse(geom.handle, _ptr(vol, "vol", torch.float32), _ptr(b, "b", torch.float32),
+                                       _ptr(ws, "ws"), ws.numel(), ctypes.byref(o),
+                                       _ptr(stats, "stats", torch.float64), _stream()))
     return vol
 
 
@@ -403,10 +409,12 @@ class Reconstructor:
             self.iterate(vol, **kw)
         return vol
 
-    def iterate_learned(self, vol: torch.Tensor, net: "Net", storage=torch.float32, n_subsets: int = 8):
+    def iterate_learned(self, vol: torch.Tensor, net: "Net", storage=torch.float32, n_subsets: int = 8,
+                        fas: bool = False):
         """Alg. 1 with the learned Landweber step on grid 0 (coarse grids plain)."""
         if self.geom.levels > 1:
-            multigrid_coarse(self.geom, vol, self.ws, n_subsets=n_subsets, stats=self.stats, storage=storage)
+            multigrid_coarse(self.geom, vol, self.ws, n_subsets=n_subsets, stats=self.stats, storage=storage,
+                             b=self.b, fas=fas)
         if not hasattr(self, "_lw_ws"):
             self._lw_ws = workspace(self.geom, WS_LANDWEBER, 0, vol.device)
             self.learned_stats = torch.zeros(8, dtype=torch.float64, device=vol.device)

@@ -86,6 +86,45 @@ def test_multigrid_c1(levels):
         assert np.sqrt(np.mean((got - truth) ** 2)) < 0.6 * np.sqrt(np.mean(truth ** 2))
 
 
+@pytest.mark.parametrize("levels", [2, 3])
+def test_multigrid_fas_c1(levels):
+    """Three iterations of the FAS variant (coarse data R(b - A mu) + A_c R mu)
+    on the 64^3 / 96^2 / 90-view workload: GPU vs oracle reconstruction RMSE
+    difference <= 1e-4 of the phantom's range."""
+    d = scan_desc(64, 96, 96, 90, 2104, levels=levels)
+    scan = oracle_scan(d)
+    og = O.level_geometry(scan, 0)
+    ph, truth = phantom(64)
+    b = O.ellipsoid_line_integrals(og, ph)
+    ref = O.reconstruct(scan, b, iters=3, levels=levels, fas=True)
+    g = gpu_geom(d)
+    rec = mgct.Reconstructor(g)
+    rec.prepare(cuda(b))
+    got = to_np(rec.reconstruct(iters=3, fas=True))
+    rng = truth.max() - truth.min()
+    rmse_diff = np.sqrt(np.mean((got - ref) ** 2)) / rng
+    assert rmse_diff <= 1e-4, rmse_diff
+
+
+def test_multigrid_fas_keeps_the_exact_solution():
+    """Consistent data b = A x (oracle) and mu = x: one FAS iteration leaves mu
+    at x up to float32 rounding; the plain recursion moves it by percents."""
+    d = scan_desc(32, 48, 48, 40, 2104, levels=2)
+    scan = oracle_scan(d)
+    _, x = phantom(32)
+    b = cuda(O.project(O.level_geometry(scan, 0), x.astype(np.float64)))
+    g = gpu_geom(d)
+    rec = mgct.Reconstructor(g)
+    rec.prepare(b)
+    moved = {}
+    for fas in (True, False):
+        v = cuda(x).clone()
+        rec.iterate(v, fas=fas)
+        moved[fas] = float((v - cuda(x)).abs().max()) / float(np.abs(x).max())
+    assert moved[True] <= 1e-4, moved
+    assert moved[False] >= 1e-2, moved
+
+
 def test_multigrid_matches_explicit_steps():
     """The native Alg. 1 driver equals the same steps issued one by one
     through the C ABI (restrict, OS-EMTR, prolong-add, Landweber)."""

@@ -129,3 +129,25 @@ def test_joint_estimation_recovers_detector_offset():
         errs.append(abs(off - 1.5))
     assert errs[-1] < 0.2 * 1.5, errs
     assert errs[-1] < errs[0], errs
+
+
+def test_geometry_grad_full_size_sampled():
+    """The drift-estimation workload at full size (256^3, 384^2 detector, 720
+    views with source/detector offsets and tilt as Gaussian random walks of
+    0.3 px per view): the gradient of all views in one call, checked at
+    sampled views against the oracle (each view's gradient depends on that
+    view alone, so the oracle runs on a scan of just those views)."""
+    from paper_2103_10329_gb300 import mgct
+    K, n, nu = 720, 256, 384
+    drift = synth.drift_walk(K, 31, sigma_px=0.3, half_diag_px=0.5 * np.sqrt(2.0) * nu)
+    d = scan_desc(n, nu, nu, K, 2104, levels=1, drift=drift)
+    g = gpu_geom(d)
+    vol = synth.voxelize_blobs(synth.blobs(6, 7, 0.05, 0.15, centre_r=0.25), n).numpy().astype(np.float32)
+    y = torch.randn((K, nu, nu), device="cuda", generator=torch.Generator("cuda").manual_seed(9))
+    got = to_np(mgct.geometry_grad(g, cuda(vol), y))
+    views = np.array([0, 233, 500, 719])
+    ds = dict(d, theta=d["theta"][views], z=d["z"][views], drift=drift[views])
+    ref = O.geometry_grad(oracle_scan(ds), vol.astype(np.float64), to_np(y[torch.as_tensor(views, device="cuda")]))
+    for j in range(5):
+        scale = np.abs(ref[:, j]).max()
+        assert np.abs(got[views, j] - ref[:, j]).max() <= 2e-4 * scale, (j, got[views, j], ref[:, j])

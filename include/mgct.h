@@ -292,7 +292,12 @@ int mgct_geometry_grad(const mgct_geom *geom, int level, int view0, int nviews, 
  * mgct_net_param_count() values in all.  mgct_net_create initialises with
  * He-normal weights from `seed`, zero biases and a zero output layer.
  * Workspaces: mgct_net_workspace_bytes(B*D*H*W, training) bytes, 256-byte
- * aligned.
+ * aligned.  mgct_net_apply (and so mgct_landweber_learned) also accepts a
+ * smaller workspace and then runs the volume in z-slabs: S planes at a time,
+ * S the largest depth with mgct_net_workspace_bytes((S + 8) H W, 0) <= the
+ * workspace, each slab computed with 4 extra planes on either side (the
+ * receptive field of the four 3x3x3 layers), so the result is the same;
+ * the RMS s is that of the whole volume.
  * ------------------------------------------------------------------------- */
 typedef struct mgct_net mgct_net;
 int mgct_net_create(uint64_t seed, mgct_net **out);

@@ -114,9 +114,15 @@ __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int 
 //                          E1 = (nv_z + c_a Ev_z)/w_a,
 // so each detector column is set up once for the thread's ZB voxels of one
 // z-column, and each voxel walks exactly the pixels where |e_z| < 1.
+// The column's quantities come from the double-float column table, and
+// both cancellations are done in double-float: e_b = pb + c_a rb - c_b, and
+// the z error is anchored at the detector row v_a nearest the thread's
+// voxels (E0 + v_a E1 - c_z, small), so that in float32 only small terms
+// remain -- the sample weights stay accurate to ~1e-7 at any N.
 template <int NCH, typename ST, bool WEIGHTED, int ZB>
-__device__ __forceinline__ void bp_view_sep(const ViewGeom &G, const BPArgs &a, int jx, int jy, int jz0,
-                                            const ST *__restrict__ sino_view, float (&acc)[ZB][NCH]) {
+__device__ __forceinline__ void bp_view_sep(const ViewGeom &G, const float4 *__restrict__ cols, const BPArgs &a,
+                                            int jx, int jy, int jz0, const ST *__restrict__ sino_view,
+                                            float (&acc)[ZB][NCH]) {
     const float X = (float)jx - G.S[0], Y = (float)jy - G.S[1];
     // with no tilt the u coordinate and depth of a point ignore its z
     const float q0 = fmaf(G.Q[1], Y, G.Q[0] * X);
@@ -127,38 +133,38 @@ __device__ __forceinline__ void bp_view_sep(const ViewGeom &G, const BPArgs &a, 
     const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
     const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
     const float ic = 0.5f * (float)(a.n - 1);
-    const float cx = (float)jx - ic, cy = (float)jy - ic, cz0 = (float)jz0 - ic;
+    const float cx = (float)jx - ic, cy = (float)jy - ic;
+    const float zm = (float)jz0 - ic + 0.5f * (float)(ZB - 1);  // centre of the thread's voxels (exact)
     for (int ju = ulo; ju <= uhi; ++ju) {
-        const float up = (float)ju - cu;
-        // identical to ray_dir() with the zero v-terms: same axis choice
-        const float wx = __fmaf_rn(up, G.Eu[0], G.Wc[0]);
-        const float wy = __fmaf_rn(up, G.Eu[1], G.Wc[1]);
-        const int ax = fabsf(wy) > fabsf(wx) ? 1 : 0;
-        const float wa = ax ? wy : wx, wb = ax ? wx : wy;
-        const float rinv = __frcp_rn(wa);
-        const float rb = wb * rinv;
-        const float *N = ax ? G.NY : G.NX;
-        const float ca = ax ? cy : cx, cb = ax ? cx : cy;
-        const float eb = fmaf(ca, rb, fmaf(up, N[1], N[0]) * rinv) - cb;
-        const float hb = 1.0f - fabsf(eb);
+        const float4 t0 = __ldg(cols + 4 * ju), t1 = __ldg(cols + 4 * ju + 1);
+        const float4 t2 = __ldg(cols + 4 * ju + 2), t3 = __ldg(cols + 4 * ju + 3);
+        const bool ay = t0.x != 0.0f;
+        const float ca = ay ? cy : cx, cb = ay ? cx : cy;
+        const DF eb = df_add(df_mul_f(DF{t0.y, t0.z}, ca), DF{t0.w, t1.x});
+        const float hb = 1.0f - fabsf(__fadd_rn(__fsub_rn(eb.hi, cb), eb.lo));
         if (hb <= 0.0f) continue;
-        const float Eb = fmaf(ca, G.Wc[2], fmaf(up, N[4], N[3])) * rinv;  // E0 + c_z
-        const float E1 = fmaf(ca, G.Ev[2], N[5]) * rinv;
+        const DF Eb = df_add(DF{t1.y, t1.z}, df_mul_f(DF{t1.w, t2.x}, ca));  // centred height at v' = 0
+        const DF E1d = df_add(DF{t2.y, t2.z}, df_mul_f(DF{t2.w, t3.x}, ca));
+        const float E1 = E1d.hi;
+        const float va = rintf((zm - Eb.hi) / E1);  // anchor row (centred units)
+        if (!(fabsf(va) < 1.0e7f)) continue;
+        const DF c = df_add(df_add(Eb, df_mul_f(E1d, va)), DF{-zm, 0.0f});
+        const float cf = c.hi + c.lo;  // z error at the anchor row for the centre voxel
         const float rE1 = 1.0f / E1;
 #pragma unroll
         for (int zz = 0; zz < ZB; ++zz) {
-            const float E0 = Eb - (cz0 + (float)zz);
-            const float t1 = (-1.0f - E0) * rE1, t2 = (1.0f - E0) * rE1;
-            const int vlo = max(0, (int)ceilf(fminf(t1, t2) + cv - 1e-3f));
-            const int vhi = min(a.nv - 1, (int)floorf(fmaxf(t1, t2) + cv + 1e-3f));
+            const float E0 = cf - ((float)zz - 0.5f * (float)(ZB - 1));
+            const float s1 = (-1.0f - E0) * rE1, s2 = (1.0f - E0) * rE1;
+            const int vlo = max(0, (int)ceilf(fminf(s1, s2) + va + cv - 1e-3f));
+            const int vhi = min(a.nv - 1, (int)floorf(fmaxf(s1, s2) + va + cv + 1e-3f));
             for (int jv = vlo; jv <= vhi; ++jv) {
                 const float vp = (float)jv - cv;
-                const float hz = 1.0f - fabsf(fmaf(vp, E1, E0));
+                const float hz = 1.0f - fabsf(fmaf(vp - va, E1, E0));
                 if (hz > 0.0f) {
                     float w = hb * hz;
                     if (!WEIGHTED) {
-                        const float rz = fmaf(vp, G.Ev[2], G.Wc[2]) * rinv;
-                        w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
+                        const float rz = fmaf(vp, t2.w, t1.w);  // (Wc_z + u' Eu_z + v' Ev_z) / w_a
+                        w *= sqrtf(fmaf(rz, rz, fmaf(t0.y, t0.y, 1.0f))) * a.h;
                     }
                     SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc[zz]);
                 }
@@ -214,7 +220,8 @@ constexpr int BPS_ZB = 4;  // voxels per thread along z (separable kernel)
 
 template <int NCH, typename ST, bool WEIGHTED>
 __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
-    k_backproject_sep(BPArgs a, const ST *__restrict__ sino, float *__restrict__ out, int accumulate) {
+    k_backproject_sep(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino, float *__restrict__ out,
+                      int accumulate) {
     __shared__ ViewGeom Gs[BP_CHUNK];
     const int jx = blockIdx.x * BP_BX + threadIdx.x;
     const int jy = blockIdx.y * BP_BY + threadIdx.y;
@@ -234,7 +241,8 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
         __syncthreads();
         if (active) {
             for (int vi = 0; vi < cn; ++vi)
-                bp_view_sep<NCH, ST, WEIGHTED, BPS_ZB>(Gs[vi], a, jx, jy, jz0,
+                bp_view_sep<NCH, ST, WEIGHTED, BPS_ZB>(Gs[vi], cols + (size_t)(a.view0 + (c0 + vi) * a.stride) * a.nu * 4,
+                                                       a, jx, jy, jz0,
                                                        sino + (size_t)(c0 + vi) * view_elems, acc);
         }
     }
@@ -375,6 +383,35 @@ __global__ void k_column_table(const ViewGeom *__restrict__ views, int K, int nu
     cols[2 * (size_t)t + 1] = make_float4(G.Wc[2] * rinv, N[5] * rinv, G.Ev[2] * rinv, 0.0f);
 }
 
+// Double-float column table (see LevelInfo::d_cols_df): same axis choice as
+// k_column_table; the quotients by w_a are taken in double-float from the
+// view table's double-float fields.
+__global__ void k_column_table_df(const ViewGeom *__restrict__ views, int K, int nu, float4 *__restrict__ cols) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K * nu) return;
+    const int k = t / nu, ju = t % nu;
+    const ViewGeom &G = views[k];
+    const float up = (float)ju - 0.5f * (float)(nu - 1);
+    const RayDir d = ray_dir(G, up, 0.0f);
+    const int ia = d.ax, ib = 1 - d.ax;
+    const DF wa = df_affine(G.Wc[ia], G.Wc_lo[ia], G.Eu[ia], G.Eu_lo[ia], G.Ev[ia], G.Ev_lo[ia], up, 0.0f);
+    const DF wb = df_affine(G.Wc[ib], G.Wc_lo[ib], G.Eu[ib], G.Eu_lo[ib], G.Ev[ib], G.Ev_lo[ib], up, 0.0f);
+    const DF rinv = df_div(DF{1.0f, 0.0f}, wa);
+    const float *N = d.ax ? G.NY : G.NX;
+    const float *Nl = d.ax ? G.NY_lo : G.NX_lo;
+    const DF rb = df_mul(wb, rinv);
+    const DF pb = df_mul(df_affine(N[0], Nl[0], N[1], Nl[1], N[2], Nl[2], up, 0.0f), rinv);
+    const DF ez0 = df_mul(df_affine(N[3], Nl[3], N[4], Nl[4], N[5], Nl[5], up, 0.0f), rinv);
+    const DF ezc = df_mul(df_affine(G.Wc[2], G.Wc_lo[2], G.Eu[2], G.Eu_lo[2], G.Ev[2], G.Ev_lo[2], up, 0.0f), rinv);
+    const DF e10 = df_mul(DF{N[5], Nl[5]}, rinv);
+    const DF e1c = df_mul(DF{G.Ev[2], G.Ev_lo[2]}, rinv);
+    float4 *o = cols + 4 * (size_t)t;
+    o[0] = make_float4(d.ax ? 1.0f : 0.0f, rb.hi, rb.lo, pb.hi);
+    o[1] = make_float4(pb.lo, ez0.hi, ez0.lo, ezc.hi);
+    o[2] = make_float4(ezc.lo, e10.hi, e10.lo, e1c.hi);
+    o[3] = make_float4(e1c.lo, 0.0f, 0.0f, 0.0f);
+}
+
 // NCH = 2 writes channel c to out + c * n^3.  WEIGHTED: the sinogram carries
 // each ray's dl already (internal solver path).
 template <int NCH, typename ST, bool WEIGHTED = false>
@@ -399,7 +436,7 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
         const int zper = BP_BZ * BPS_ZB;
         dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + zper - 1) / zper);
         MGCT_KERNEL(KK_BACKPROJECT, s,
-                    k_backproject_sep<NCH, ST, WEIGHTED><<<grid, dim3(BP_BX, BP_BY, BP_BZ), 0, s>>>(a, sino, out, accumulate));
+                    k_backproject_sep<NCH, ST, WEIGHTED><<<grid, dim3(BP_BX, BP_BY, BP_BZ), 0, s>>>(a, L.d_cols_df, sino, out, accumulate));
     } else {
         dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + BP_BZ - 1) / BP_BZ);
         MGCT_KERNEL(KK_BACKPROJECT, s,

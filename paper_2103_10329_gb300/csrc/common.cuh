@@ -61,6 +61,7 @@ struct LevelInfo {
     double h, pitch;
     ViewGeom *d_views;  // device [K]
     float4 *d_cols;     // device [K][nu][2] detector-column table (separable geometries), or NULL
+    float4 *d_cols_df;  // device [K][nu][4] the same quantities in double-float, or NULL
 };
 
 // Detector-column table of a separable geometry (no detector tilt): for view
@@ -71,6 +72,11 @@ struct LevelInfo {
 //   e_b = c_a rb + pb - c_b,   E0 + c_z = ez0 + c_a ezc,   E1 = e10 + c_a e1c.
 // Entry: {ax, rb, pb, ez0}, {ezc, e10, e1c, 0}.
 int launch_column_table(const mgct_geom *g, int level, cudaStream_t s);
+// The same column quantities as double-float pairs (hi, lo), for the public
+// back-projector's accuracy at large N: entry {ax, rb, rb_lo, pb},
+// {pb_lo, ez0, ez0_lo, ezc}, {ezc_lo, e10, e10_lo, e1c}, {e1c_lo, 0, 0, 0}
+// (centred: E0 + c_z = ez0 + c_a ezc).
+int launch_column_table_df(const mgct_geom *g, int level, cudaStream_t s);
 
 }  // namespace mgct
 
@@ -197,6 +203,13 @@ __device__ __forceinline__ DF df_mul_f(DF x, float f) {
     float p = __fmul_rn(x.hi, f);
     float e = __fmaf_rn(x.hi, f, -p);
     e = __fmaf_rn(x.lo, f, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
     return quick_two_sum(p, e);
 }
 __device__ __forceinline__ DF df_div(DF x, DF y) {

@@ -211,7 +211,11 @@ static int upload_tables(mgct_geom *g) {
         if (!g->separable) continue;
         if (!L.d_cols)
             MGCT_TRY(check_cuda(cudaMalloc(&L.d_cols, (size_t)K * L.nu * 2 * sizeof(float4)), "allocate column table"));
+        if (!L.d_cols_df)
+            MGCT_TRY(check_cuda(cudaMalloc(&L.d_cols_df, (size_t)K * L.nu * 4 * sizeof(float4)),
+                                "allocate column table"));
         MGCT_TRY(launch_column_table(g, l, 0));
+        MGCT_TRY(launch_column_table_df(g, l, 0));
     }
     return check_cuda(cudaDeviceSynchronize(), "column tables");
 }
@@ -251,6 +255,7 @@ void mgct_geometry_destroy(mgct_geom *g) {
     for (int l = 0; l < 8; ++l) {
         if (g->lev[l].d_views) cudaFree(g->lev[l].d_views);
         if (g->lev[l].d_cols) cudaFree(g->lev[l].d_cols);
+        if (g->lev[l].d_cols_df) cudaFree(g->lev[l].d_cols_df);
     }
     if (g->d_scratch_vol) cudaFree(g->d_scratch_vol);
     if (g->d_scratch_quads) cudaFree(g->d_scratch_quads);

@@ -59,10 +59,12 @@ __global__ void k_pack_weights(const float *__restrict__ w, __nv_bfloat16 *__res
 }
 
 // x (float32 [nvox]) scaled by 1/s into channel 0 of a 16-channel bf16 tensor;
-// s = sqrt(sumsq / nvox) from a device scalar (or 1 when scale == NULL).
-__global__ void k_net_input(const float *__restrict__ x, const double *__restrict__ sumsq, int nvox,
+// s = sqrt(sumsq / nnorm) from a device scalar (or 1 when sumsq == NULL);
+// nnorm is the voxel count of the whole volume the sum was taken over (a
+// z-slab of it may be processed here).
+__global__ void k_net_input(const float *__restrict__ x, const double *__restrict__ sumsq, double nnorm, int nvox,
                             __nv_bfloat16 *__restrict__ x0, float *__restrict__ xs) {
-    const float inv = sumsq ? (float)(1.0 / fmax(sqrt(sumsq[0] / (double)nvox), 1e-30)) : 1.0f;
+    const float inv = sumsq ? (float)(1.0 / fmax(sqrt(sumsq[0] / nnorm), 1e-30)) : 1.0f;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nvox; p += gridDim.x * blockDim.x) {
         const float v = x[p] * inv;
         if (xs) xs[p] = v;
@@ -79,8 +81,8 @@ __global__ void k_net_input(const float *__restrict__ x, const double *__restric
 // (NaN everywhere when a convolution of this pass failed, so that the
 // learned step's line search rejects it)
 __global__ void k_net_output(const float *__restrict__ x, const float *__restrict__ y, const double *__restrict__ sumsq,
-                             int nvox, const int *__restrict__ err, float *__restrict__ out) {
-    const float s = *err ? __int_as_float(0x7fc00000) : (float)fmax(sqrt(sumsq[0] / (double)nvox), 1e-30);
+                             double nnorm, int nvox, const int *__restrict__ err, float *__restrict__ out) {
+    const float s = *err ? __int_as_float(0x7fc00000) : (float)fmax(sqrt(sumsq[0] / nnorm), 1e-30);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nvox; p += gridDim.x * blockDim.x)
         out[p] = s * (x[p] + y[p]);
 }
@@ -211,7 +213,8 @@ static int conv_bwd_data(int l, const ConvArgs &a, int *err, cudaStream_t s) {
     }
 }
 
-constexpr int WG_BLOCKS = 96;  // voxel-tile groups per tap in the weight gradient
+constexpr int WG_BLOCKS = 96;
+constexpr int NET_HALO = 4;  // planes each side a slab needs: four 3x3x3 layers  // voxel-tile groups per tap in the weight gradient
 
 template <int CIN, int COUT>
 static int conv_wgrad_t(const __nv_bfloat16 *in, const __nv_bfloat16 *gout, float *part, int B, int D, int H, int W,
@@ -407,15 +410,12 @@ int mgct_net_create(uint64_t seed, mgct_net **out) {
 // forward pass on [B][D][H][W] voxels; x float32 [nvox]; scale: when
 // `normalise`, x is divided by its RMS (computed here).  Leaves the
 // activations in the workspace.
-static int net_forward(const mgct_net *net, int B, int D, int H, int W, const float *x, bool normalise,
-                       const NetSpace &sp, cudaStream_t s) {
+// ss: device sum of squares of the whole volume (x is scaled by 1 / RMS with
+// RMS = sqrt(ss / nnorm)), or NULL for no scaling.
+static int net_forward(const mgct_net *net, int B, int D, int H, int W, const float *x, const double *ss,
+                       double nnorm, const NetSpace &sp, cudaStream_t s) {
     const int nvox = B * D * H * W;
-    const double *ss = nullptr;
-    if (normalise) {
-        MGCT_TRY(net_sumsq(x, nvox, sp.sumsq, sp.lpart, s));
-        ss = sp.sumsq;
-    }
-    MGCT_KERNEL(KK_CONV, s, k_net_input<<<std::min((nvox + 255) / 256, 152 * 32), 256, 0, s>>>(x, ss, nvox, sp.x0, sp.xs));
+    MGCT_KERNEL(KK_CONV, s, k_net_input<<<std::min((nvox + 255) / 256, 152 * 32), 256, 0, s>>>(x, ss, nnorm, nvox, sp.x0, sp.xs));
     const __nv_bfloat16 *cur = sp.x0;
     for (int l = 0; l < NL; ++l) {
         ConvArgs a;
@@ -478,14 +478,42 @@ int mgct_net_apply(const mgct_net *net, int B, int D, int H, int W, const float 
     MGCT_TRY(check_ptr(ws, "workspace"));
     if (B < 1 || D < 1 || H < 1 || W < 1 || (int64_t)B * D * H * W > ((int64_t)1 << 31) - 1)
         return set_error(MGCT_ESHAPE, "bad volume dimensions");
-    const int64_t nvox = (int64_t)B * D * H * W;
-    if (reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < mgct_net_workspace_bytes(nvox, 0))
-        return set_error(MGCT_ENOMEM, "net workspace too small or misaligned");
-    NetSpace sp;
-    carve_net(nvox, false, static_cast<char *>(ws), &sp);
+    const int64_t nvox = (int64_t)B * D * H * W, plane = (int64_t)H * W;
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return set_error(MGCT_EALIGN, "net workspace must be 256-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    MGCT_TRY(net_forward(net, B, D, H, W, dir, true, sp, s));
-    MGCT_KERNEL(KK_CONV, s, k_net_output<<<std::min((int)((nvox + 255) / 256), 152 * 32), 256, 0, s>>>(sp.xs, sp.y, sp.sumsq, (int)nvox, net->err, out));
+    NetSpace sp;
+    if (ws_bytes >= mgct_net_workspace_bytes(nvox, 0)) {
+        carve_net(nvox, false, static_cast<char *>(ws), &sp);
+        MGCT_TRY(net_sumsq(dir, (int)nvox, sp.sumsq, sp.lpart, s));
+        MGCT_TRY(net_forward(net, B, D, H, W, dir, sp.sumsq, (double)nvox, sp, s));
+        MGCT_KERNEL(KK_CONV, s, k_net_output<<<std::min((int)((nvox + 255) / 256), 152 * 32), 256, 0, s>>>(
+                                    sp.xs, sp.y, sp.sumsq, (double)nvox, (int)nvox, net->err, out));
+        return MGCT_OK;
+    }
+    // z-slabs of S planes, each computed on S + 2 NET_HALO planes: the four
+    // 3x3x3 layers see NET_HALO planes on each side, so the slab's own planes
+    // are exact (at the volume's faces the zero padding is the volume's own)
+    int S = 0;
+    for (int t = D; t >= 1; t = t > 64 ? t - t / 8 : t - 1)
+        if (mgct_net_workspace_bytes(std::min<int64_t>(t + 2 * NET_HALO, D) * plane, 0) <= ws_bytes) {
+            S = t;
+            break;
+        }
+    if (S < 1) return set_error(MGCT_ENOMEM, "net workspace too small for one slab");
+    carve_net(std::min<int64_t>(S + 2 * NET_HALO, D) * plane, false, static_cast<char *>(ws), &sp);
+    MGCT_TRY(net_sumsq(dir, (int)nvox, sp.sumsq, sp.lpart, s));
+    for (int b = 0; b < B; ++b) {
+        for (int z0 = 0; z0 < D; z0 += S) {
+            const int z1 = std::min(D, z0 + S);
+            const int zs = std::max(0, z0 - NET_HALO), ze = std::min(D, z1 + NET_HALO);
+            const int64_t base = ((int64_t)b * D + zs) * plane;
+            MGCT_TRY(net_forward(net, 1, ze - zs, H, W, dir + base, sp.sumsq, (double)nvox, sp, s));
+            const int64_t off = (int64_t)(z0 - zs) * plane, cnt = (int64_t)(z1 - z0) * plane;
+            MGCT_KERNEL(KK_CONV, s, k_net_output<<<std::min((int)((cnt + 255) / 256), 152 * 32), 256, 0, s>>>(
+                                        sp.xs + off, sp.y + off, sp.sumsq, (double)nvox, (int)cnt, net->err,
+                                        out + ((int64_t)b * D + z0) * plane));
+        }
+    }
     return MGCT_OK;
 }
 
@@ -504,7 +532,7 @@ int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const f
     carve_net(nvox, true, static_cast<char *>(ws), &sp);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // x and t are already in scaled units
-    MGCT_TRY(net_forward(net, B, D, H, W, x, false, sp, s));
+    MGCT_TRY(net_forward(net, B, D, H, W, x, nullptr, 1.0, sp, s));
     const int nb = std::min(1024, (nvox + 255) / 256);
     MGCT_KERNEL(KK_CONV, s, k_mse<<<nb, 256, 0, s>>>(sp.xs, sp.y, t, nvox, net->err, sp.g[NL - 1], sp.lpart));
     MGCT_TRY(launch_sum_partials(sp.lpart, nb, 1, net->loss, s));

@@ -26,6 +26,14 @@ int launch_scaled_copy(size_t count, const float *d, const double *alpha, float 
 int launch_update_choice(size_t count, float *mu, const float *d, const float *dl, const double *st, float lam,
                          cudaStream_t s);
 int launch_axpy(size_t count, float a, const float *x, float *y, cudaStream_t s);
+int launch_column_table_df(const mgct_geom *g, int level, cudaStream_t s) {
+    const LevelInfo &L = g->lev[level];
+    const int K = g->desc.n_views;
+    const int total = K * L.nu;
+    MGCT_KERNEL(KK_OTHER, s, k_column_table_df<<<(total + 255) / 256, 256, 0, s>>>(L.d_views, K, L.nu, L.d_cols_df));
+    return MGCT_OK;
+}
+
 int launch_column_table(const mgct_geom *g, int level, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
     const int K = g->desc.n_views;

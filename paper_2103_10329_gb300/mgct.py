@@ -369,7 +369,7 @@ def landweber_learned(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, net: "
         ws = workspace(geom, WS_LANDWEBER, level, vol.device)
     if stats is None:
         stats = torch.zeros(8, dtype=torch.float64, device=vol.device)
-    nws = net._workspace(vol.numel(), False)
+    nws = net._workspace(vol.numel(), False, plane=int(vol.shape[-1] * vol.shape[-2]))
     o = _opts(None, lam, True, 0, storage)
     _check(lib().mgct_landweber_learned(geom.handle, level, _ptr(vol, "vol", torch.float32),
                                         _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(), ctypes.byref(o),
@@ -496,18 +496,33 @@ class Net:
         _check(_net_sigs().mgct_net_get_grads(self.handle, out.ctypes.data, self.count))
         return out
 
-    def _workspace(self, nvox: int, training: bool) -> torch.Tensor:
-        need = int(_net_sigs().mgct_net_workspace_bytes(nvox, 1 if training else 0))
-        if self._ws is None or self._ws.numel() < need:
-            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-        return self._ws
+    # inference workspaces above this size are replaced by a z-slab workspace
+    # (mgct_net_apply then runs the volume slab by slab)
+    SLAB_BYTES = 16 << 30
 
-    def apply(self, step: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-        """Corrected step s (x + f(x)), x = step / RMS(step); step [B][D][H][W] or [D][H][W]."""
+    def _workspace(self, nvox: int, training: bool, plane: int | None = None,
+                   slab_planes: int | None = None) -> torch.Tensor:
+        L = _net_sigs()
+        need = int(L.mgct_net_workspace_bytes(nvox, 1 if training else 0))
+        if not training and plane and (slab_planes is not None or need > self.SLAB_BYTES):
+            if slab_planes is None:
+                per_plane = int(L.mgct_net_workspace_bytes(plane, 0))
+                slab_planes = max(1, self.SLAB_BYTES // per_plane - 8)
+            need = min(need, int(L.mgct_net_workspace_bytes((slab_planes + 8) * plane, 0)))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = None
+            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        return self._ws[:need]
+
+    def apply(self, step: torch.Tensor, out: torch.Tensor | None = None,
+              slab_planes: int | None = None) -> torch.Tensor:
+        """Corrected step s (x + f(x)), x = step / RMS(step); step [B][D][H][W] or [D][H][W].
+        Volumes whose workspace would exceed SLAB_BYTES (or any volume, with
+        slab_planes) run in z-slabs of that many planes plus a 4-plane halo."""
         shp = step.shape if step.dim() == 4 else (1,) + tuple(step.shape)
         if out is None:
             out = torch.empty_like(step)
-        ws = self._workspace(int(np.prod(shp)), False)
+        ws = self._workspace(int(np.prod(shp)), False, plane=int(shp[2] * shp[3]), slab_planes=slab_planes)
         _check(_net_sigs().mgct_net_apply(self.handle, *shp, _ptr(step, "step", torch.float32),
                                           _ptr(out, "out", torch.float32), _ptr(ws, "ws"), ws.numel(), _stream()))
         return out

@@ -260,3 +260,27 @@ def test_restrict_and_prolong():
     ref = fine.astype(np.float64) + O.prolong(cn.astype(np.float64) - co.astype(np.float64))
     got = to_np(mgct.prolong_add(cuda(cn), cuda(co), cuda(fine)))
     assert np.abs(got - ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("cfg", [(256, 384, 720), (512, 768, 1440)], ids=["c2", "c3"])
+def test_solver_backprojection_full_size_sampled(cfg):
+    """The solver's own A^T (the dl-weighted residual written by the
+    projector's epilogue, then the slab back-projector), in the launch
+    configuration the bench times: with mu = 0 and no filter the Landweber
+    direction is alpha A^T b, so A^T b = step / alpha; sampled voxels
+    against the oracle."""
+    n, nu, nviews = cfg
+    d = scan_desc(n, nu, nu, nviews, 2104, levels=1)
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    y = torch.rand((nviews, nu, nu), device="cuda", generator=torch.Generator("cuda").manual_seed(6))
+    stats = torch.zeros(4, dtype=torch.float64, device="cuda")
+    step = mgct.landweber_direction(g, torch.zeros((n, n, n), device="cuda"), y, precond=False, stats=stats)
+    alpha = float(stats[0])
+    assert alpha > 0
+    vox = synth.random_indices(24, (n, n, n), 7)
+    vi = torch.as_tensor(vox, device="cuda", dtype=torch.long)
+    got = to_np(step[vi[:, 2], vi[:, 1], vi[:, 0]]) / alpha
+    ref = O.backproject_voxels(og, to_np(y), vox, radius=5)
+    e = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * float(step.abs().max()) / alpha)
+    assert e.max() <= TOL_F32, summary(e)

@@ -257,8 +257,6 @@ template <typename T, typename SRC = float>
 int launch_build_quads(int n, const SRC *src, void *dst, cudaStream_t s);
 template <typename T>
 int launch_transpose_xy(int n, const T *in, T *out, cudaStream_t s);
-template <typename T>
-int launch_cast_transpose(int n, const float *in, T *out, T *outT, cudaStream_t s);
 
 int launch_sum_partials(const double *part, int count, int nvals, double *out, cudaStream_t s);
 

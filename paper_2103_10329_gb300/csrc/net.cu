@@ -6,8 +6,10 @@
 // channel; its input is the step alpha d scaled to unit RMS, x = alpha d / s,
 // and the corrected step is d' = s (x + f(x)).  Training minimises the mean
 // of (x + f(x) - t)^2 with t = e / s, e the error of the current estimate, by
-// Adam on float32 master weights; the convolutions run on BF16 tensor cores
-// with float32 accumulation and BF16 activations.
+// Adam on float32 master weights.  The convolutions run on the BF16 tensor
+// cores with float32 accumulation and BF16 activations: forward and
+// backward-data on tcgen05 (conv3d_tc.cuh), the weight gradient on mma.sync
+// (conv3d.cuh).
 #include <cmath>
 #include <cstring>
 #include <random>

@@ -1,7 +1,8 @@
-// Streaming volume and sinogram kernels: transpose, the Eq. 5 preconditioner,
-// restriction and prolongation (Alg. 1), the Landweber update with soft
-// thresholding, and deterministic float64 reductions.  All are bound by HBM
-// bandwidth; each reads and writes its arrays once with coalesced accesses.
+// Streaming volume and sinogram kernels: transpose and the projector's quad
+// copies, the Eq. 5 preconditioner, restriction and prolongation (Alg. 1),
+// the Landweber update with soft thresholding, and deterministic float64
+// reductions.  All are bound by HBM bandwidth; each reads and writes its
+// arrays once with coalesced accesses.
 #include <type_traits>
 
 #include "common.cuh"
@@ -38,40 +39,6 @@ template int launch_transpose_xy<float>(int, const float *, float *, cudaStream_
 template int launch_transpose_xy<__nv_bfloat16>(int, const __nv_bfloat16 *, __nv_bfloat16 *, cudaStream_t);
 template int launch_transpose_xy<__half>(int, const __half *, __half *, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// float32 vol [z][y][x] -> 16-bit copies out [z][y][x] and outT [z][x][y]
-// (the projector's two read layouts), one pass through a shared tile
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_cast_transpose(int n, const float *__restrict__ in, T *__restrict__ out,
-                                                        T *__restrict__ outT) {
-    __shared__ float tile[32][33];
-    const int z = blockIdx.z;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    const size_t slab = (size_t)z * n * n;
-    for (int dy = threadIdx.y; dy < 32; dy += 8) {
-        int x = x0 + threadIdx.x, y = y0 + dy;
-        if (x < n && y < n) {
-            float v = in[slab + (size_t)y * n + x];
-            tile[dy][threadIdx.x] = v;
-            out[slab + (size_t)y * n + x] = from_f32<T>(v);
-        }
-    }
-    __syncthreads();
-    for (int dx = threadIdx.y; dx < 32; dx += 8) {
-        int y = y0 + threadIdx.x, x = x0 + dx;
-        if (x < n && y < n) outT[slab + (size_t)x * n + y] = from_f32<T>(tile[threadIdx.x][dx]);
-    }
-}
-
-template <typename T>
-int launch_cast_transpose(int n, const float *in, T *out, T *outT, cudaStream_t s) {
-    dim3 grid((n + 31) / 32, (n + 31) / 32, n);
-    MGCT_KERNEL(KK_TRANSPOSE, s, k_cast_transpose<T><<<grid, dim3(32, 8), 0, s>>>(n, in, out, outT));
-    return MGCT_OK;
-}
-template int launch_cast_transpose<__nv_bfloat16>(int, const float *, __nv_bfloat16 *, __nv_bfloat16 *, cudaStream_t);
-template int launch_cast_transpose<__half>(int, const float *, __half *, __half *, cudaStream_t);
 
 // two float32 values rounded to 16 bits, packed low then high
 __device__ __forceinline__ uint32_t pack2(float lo, float hi, __nv_bfloat16) {

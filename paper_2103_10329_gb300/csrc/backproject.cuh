@@ -274,13 +274,16 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
 // columns, so the pixel reads of a warp fall on one detector row.
 constexpr int BS_TX = 32, BS_TY = 4, BS_THREADS = BS_TX * BS_TY;
 
+#ifndef MGCT_BS_PAIRS
+#define MGCT_BS_PAIRS 1
+#endif
 template <int NCH>
 struct SlabCfg {
     // voxels per slab: 16 keeps the shared slab at 10 KB so that 16 blocks
     // (64 warps) fit per SM; measured 64 -> 32 -> 16: 74 -> 63 -> 55 ms per
     // grid-0 launch at 256^3 / 720 views
     static constexpr int Z = 16 / NCH;
-    static constexpr int ROWS = Z + 4;  // two guard rows at each end
+    static constexpr int ROWS = Z + 5;  // guard rows: two below, three above (row pairs reach r + 2)
 };
 
 template <int NCH, typename ST>
@@ -329,7 +332,28 @@ __global__ void __launch_bounds__(BS_THREADS)
                 const int vhi = min(a.nv - 1, (int)floorf(fmaxf(ta, tb) + 1e-3f));
                 float vf = (float)vlo - cv;
                 const ST *__restrict__ px = sv + (size_t)vlo * a.nu + ju;
-                for (int jv = vlo; jv <= vhi; ++jv, vf += 1.0f, px += a.nu) {
+                int jv = vlo;
+                if constexpr (NCH == 1) {
+                  if (MGCT_BS_PAIRS && E1 > 0.0f && E1 < 0.999f) {
+                    // two rows at a time: their crossings floor(fz) are equal or
+                    // one apart (0 < E1 < 1), so the pair touches three slab
+                    // rows r, r + 1, r + 2 -- three read-modify-writes, not four
+                    for (; jv + 1 <= vhi; jv += 2, vf += 2.0f, px += 2 * (size_t)a.nu) {
+                        const float fz0 = fmaf(vf, E1, E0), fz1 = fmaf(vf + 1.0f, E1, E0);
+                        const float fl0 = floorf(fz0), fl1 = floorf(fz1);
+                        const float t0 = fz0 - fl0, t1 = fz1 - fl1;
+                        const int r = min(max((int)fl0 - z0 + 2, 0), ROWS - 3);
+                        const bool same = fl1 == fl0;
+                        const float y0 = hb * to_f32(__ldg(px)), y1 = hb * to_f32(__ldg(px + a.nu));
+                        const float a0 = y0 * t0, b0 = y1 * t1;
+                        const float lo1 = y1 - b0;
+                        acc[0][r][tid] += (y0 - a0) + (same ? lo1 : 0.0f);
+                        acc[0][r + 1][tid] += a0 + (same ? b0 : lo1);
+                        if (!same) acc[0][r + 2][tid] += b0;
+                    }
+                  }
+                }
+                for (; jv <= vhi; ++jv, vf += 1.0f, px += a.nu) {
                     const float fz = fmaf(vf, E1, E0);
                     const float fl = floorf(fz);
                     const float t = fz - fl;

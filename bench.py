@@ -390,6 +390,52 @@ def literal_tta(rec, g, truth, net, workload=None, target=1e-3, cap=50):
     return out
 
 
+def hbm_kernel_rates(peak_gbs, n=512, reps=5):
+    """The HBM-bound kernels of the step, each through the C ABI on arrays
+    larger than L2 (512^3 float32 = 537 MB): achieved GB/s from algorithmic
+    bytes (each array read or written once) over the CUDA-event time of one
+    launch (median of `reps`, after two warm-up launches)."""
+    import torch
+    from paper_2103_10329_gb300 import mgct, synth
+    dev = "cuda"
+    g = torch.Generator(device=dev).manual_seed(1)
+    x = torch.rand((n, n, n), device=dev, generator=g)
+    y = torch.rand((n, n, n), device=dev, generator=g)
+    o = torch.empty_like(x)
+    c1 = torch.rand((n // 2,) * 3, device=dev, generator=g)
+    c0 = torch.rand((n // 2,) * 3, device=dev, generator=g)
+    kv, nvs = 360, 2 * n  # a sinogram of 360 views of (2n)^2 pixels: 1.5 GB
+    sino = torch.rand((kv, nvs, nvs), device=dev, generator=g)
+    th, z = synth.trajectory(2, 1)
+    geom = mgct.Geometry(n, 16, 16, th, z, synth.default_pitch(16), levels=1)
+    vox = n ** 3
+    cases = {
+        "precondition (Eq. 5 stencil)": (lambda: mgct.precondition(geom, x, out=o), 8.0 * vox),
+        "update y += a x": (lambda: mgct.axpy(0.5, x, y), 12.0 * vox),
+        "restrict_volume (2x2x2 mean)": (lambda: mgct.restrict_volume(x, out=c1), 4.5 * vox),
+        "prolong_add (trilinear)": (lambda: mgct.prolong_add(c1, c0, y), 9.0 * vox),
+        "restrict_sino (2x2 mean)": (lambda: mgct.restrict_sino(sino), 5.0 * kv * nvs * nvs),
+    }
+    out = {}
+    for name, (fn, nbytes) in cases.items():
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = sorted(ts)[len(ts) // 2]
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "bytes_alg": nbytes, "gbs": gbs, "frac_of_measured_hbm": gbs / peak_gbs}
+    geom.close()
+    return {"size": f"{n}^3 volumes (537 MB, larger than L2), sinogram {kv} x {nvs}^2", "peak_gbs": peak_gbs,
+            "kernels": out}
+
+
 def gpu_arm(args, rank, world):
     import torch
     from paper_2103_10329_gb300 import build, mgct
@@ -609,6 +655,10 @@ def gpu_arm(args, rank, world):
             }
             rec.prepare(b)
 
+    hbm = None
+    if not args.no_hbm and rank == 0:
+        hbm = hbm_kernel_rates(peaks.get("hbm_gbs", 6790.0))
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -625,7 +675,7 @@ def gpu_arm(args, rank, world):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(workload_config(args.workload), parallelism=f"replicas x{world}"),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "kernels": kernels, "time_to_accuracy": tta}
+                "clocks": clk, "kernels": kernels, "hbm_kernels": hbm, "time_to_accuracy": tta}
         print(json.dumps(line), flush=True)
     g.close()
 
@@ -643,6 +693,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-views", type=int, default=8)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-hbm", action="store_true", help="skip the HBM-bound kernel rates at 512^3")
     ap.add_argument("--no-literal", action="store_true",
                     help="skip the seconds-to-RMSE<=1e-3 runs on inverse-crime data")
     ap.add_argument("--learn-phantoms", type=int, default=96)

@@ -104,7 +104,7 @@ struct Stencil27 {
 constexpr int ST_BX = 32, ST_BY = 8, ST_ZB = 16;
 
 __global__ void __launch_bounds__(ST_BX *ST_BY)
-    k_precondition(int n, Stencil27 K, const float *__restrict__ in, float *__restrict__ out) {
+    k_precondition_generic(int n, Stencil27 K, const float *__restrict__ in, float *__restrict__ out) {
     __shared__ float pl[3][ST_BY + 2][ST_BX + 2];
     const int x0 = blockIdx.x * ST_BX, y0 = blockIdx.y * ST_BY, z0 = blockIdx.z * ST_ZB;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * ST_BX;
@@ -161,9 +161,137 @@ static Stencil27 eq5_stencil(int slice_axis) {
     return K;
 }
 
+// ---------------------------------------------------------------------------
+// Eq. 5 with its slices along z (the default reading), as an HBM stream.
+// The two outer slices are the same 3x3 matrix (-1 everywhere but a 0 centre)
+// and the middle one is (-8 corners, -4 edges, 64 centre), all over 64, so
+// with, in one z plane, c = the centre, e = the sum of the 4 edge and k =
+// of the 4 corner neighbours,
+//   a(z) = -(e + k) / 64,   b(z) = c - e / 16 - k / 8,
+//   out(z) = a(z - 1) + b(z) + a(z + 1).
+// A block owns a 128 x 8 column of the volume over PZ_ZB planes; the planes
+// (with a one-voxel x/y halo, zero outside) stream through a PZ_ST-deep ring
+// of shared-memory slots by cp.async, each is read from shared memory once
+// (a float4 per thread and row, the x neighbours by lane shuffles), and a, b
+// roll in registers.  Every input element is read from HBM about once.
+// ---------------------------------------------------------------------------
+constexpr int PZ_TX = 128, PZ_TY = 8, PZ_ZB = 32, PZ_ST = 4, PZ_W = 136;  // slot row: x0-1 at column 3
+
+__device__ __forceinline__ uint32_t sh_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cpa4(float *dst, const float *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sh_addr(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa16(float *dst, const float *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sh_addr(dst)), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__global__ void __launch_bounds__(PZ_TX / 4 * PZ_TY) k_precondition_z(int n, const float *__restrict__ in,
+                                                                      float *__restrict__ out) {
+    __shared__ __align__(16) float pl[PZ_ST][PZ_TY + 2][PZ_W];
+    const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+    const int x0 = blockIdx.x * PZ_TX, y0 = blockIdx.y * PZ_TY, z0 = blockIdx.z * PZ_ZB;
+    const int zend = min(n, z0 + PZ_ZB);
+    const int P = zend - z0 + 2;  // planes z0 - 1 .. zend
+    const size_t nn = (size_t)n * n;
+    const bool vec = (n & 3) == 0;
+    auto load = [&](int q) {  // plane z0 - 1 + q into slot q % PZ_ST
+        const int p = z0 - 1 + q;
+        float(*dst)[PZ_W] = pl[q % PZ_ST];
+        const bool zok = p >= 0 && p < n;
+        const float *src = in + (zok ? (size_t)p * nn : 0);
+        if (vec) {
+            for (int e = tid; e < (PZ_TY + 2) * (PZ_TX / 4); e += PZ_TX / 4 * PZ_TY) {
+                const int ly = e / (PZ_TX / 4), c4 = e % (PZ_TX / 4);
+                const int y = y0 + ly - 1, x = x0 + 4 * c4;
+                const bool ok = zok && y >= 0 && y < n && x < n;
+                cpa16(&dst[ly][4 + 4 * c4], ok ? src + (size_t)y * n + x : in, ok ? 16 : 0);
+            }
+            for (int e = tid; e < (PZ_TY + 2) * 2; e += PZ_TX / 4 * PZ_TY) {
+                const int ly = e >> 1, side = e & 1;
+                const int y = y0 + ly - 1, x = side ? x0 + PZ_TX : x0 - 1;
+                const bool ok = zok && y >= 0 && y < n && x >= 0 && x < n;
+                cpa4(&dst[ly][side ? 4 + PZ_TX : 3], ok ? src + (size_t)y * n + x : in, ok);
+            }
+        } else {
+            for (int e = tid; e < (PZ_TY + 2) * (PZ_TX + 2); e += PZ_TX / 4 * PZ_TY) {
+                const int ly = e / (PZ_TX + 2), lx = e % (PZ_TX + 2);
+                const int y = y0 + ly - 1, x = x0 + lx - 1;
+                const bool ok = zok && y >= 0 && y < n && x >= 0 && x < n;
+                cpa4(&dst[ly][lx + 3], ok ? src + (size_t)y * n + x : in, ok);
+            }
+        }
+    };
+    // PZ_ST - 1 groups in flight from the start (empty ones past the end), so
+    // that plane q has landed when at most PZ_ST - 2 groups are pending
+    for (int q = 0; q < PZ_ST - 1; ++q) {
+        if (q < P) load(q);
+        cpa_commit();
+    }
+    const int y = y0 + ty, xb = x0 + 4 * lane;
+    float A2[4] = {0.f, 0.f, 0.f, 0.f}, A1[4] = {0.f, 0.f, 0.f, 0.f}, B1[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < P; ++q) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(PZ_ST - 2) : "memory");
+        __syncthreads();  // plane q visible; every thread is past plane q - 1, whose slot is refilled next
+        if (q + PZ_ST - 1 < P) load(q + PZ_ST - 1);
+        cpa_commit();
+        const float(*S)[PZ_W] = pl[q % PZ_ST];
+        float lr[3][4], cc[3][4];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float4 v = *reinterpret_cast<const float4 *>(&S[ty + r][4 + 4 * lane]);
+            float left = __shfl_up_sync(0xffffffffu, v.w, 1), right = __shfl_down_sync(0xffffffffu, v.x, 1);
+            if (lane == 0) left = S[ty + r][3];
+            if (lane == 31) right = S[ty + r][4 + PZ_TX];
+            const float e[6] = {left, v.x, v.y, v.z, v.w, right};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                lr[r][j] = e[j] + e[j + 2];
+                cc[r][j] = e[j + 1];
+            }
+        }
+        float a[4], b[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float k = lr[0][j] + lr[2][j];
+            const float ed = (cc[0][j] + cc[2][j]) + lr[1][j];
+            a[j] = -(ed + k) * (1.0f / 64.0f);
+            b[j] = cc[1][j] - ed * (1.0f / 16.0f) - k * (1.0f / 8.0f);
+        }
+        if (q >= 2 && y < n) {
+            const int z = z0 + q - 2;
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = A2[j] + B1[j] + a[j];
+            float *dst = out + (size_t)z * nn + (size_t)y * n + xb;
+            if (vec) {
+                if (xb < n) *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (xb + j < n) dst[j] = o[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            A2[j] = A1[j];
+            A1[j] = a[j];
+            B1[j] = b[j];
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 int launch_precondition(int n, int slice_axis, const float *in, float *out, cudaStream_t s) {
+    if (slice_axis == 2) {
+        dim3 grid((n + PZ_TX - 1) / PZ_TX, (n + PZ_TY - 1) / PZ_TY, (n + PZ_ZB - 1) / PZ_ZB);
+        MGCT_KERNEL(KK_PRECONDITION, s, k_precondition_z<<<grid, PZ_TX / 4 * PZ_TY, 0, s>>>(n, in, out));
+        return MGCT_OK;
+    }
     dim3 grid((n + ST_BX - 1) / ST_BX, (n + ST_BY - 1) / ST_BY, (n + ST_ZB - 1) / ST_ZB);
-    MGCT_KERNEL(KK_PRECONDITION, s, k_precondition<<<grid, dim3(ST_BX, ST_BY), 0, s>>>(n, eq5_stencil(slice_axis), in, out));
+    MGCT_KERNEL(KK_PRECONDITION, s,
+                k_precondition_generic<<<grid, dim3(ST_BX, ST_BY), 0, s>>>(n, eq5_stencil(slice_axis), in, out));
     return MGCT_OK;
 }
 
@@ -204,32 +332,59 @@ __global__ void k_restrict_sino(int k, int nvc, int nuc, const float2 *__restric
 
 // fine[2n]^3 += P(new - old): per axis the fine cell 2i takes 3/4 of coarse i
 // and 1/4 of coarse i-1, the cell 2i+1 3/4 of i and 1/4 of i+1 (clamped).
-__global__ void k_prolong_add(int nc, const float *__restrict__ cn, const float *__restrict__ co,
-                              float *__restrict__ fine) {
+// Thread = one coarse cell (i, j, k) and its 2 x 2 x 2 fine cells: the 27
+// coarse differences around it are read once (through L1) and the weights
+// applied axis by axis; the fine cells are four float2 read-modify-writes.
+__global__ void __launch_bounds__(128) k_prolong_add(int nc, const float *__restrict__ cn,
+                                                     const float *__restrict__ co, float *__restrict__ fine) {
     const int nf = 2 * nc;
-    const size_t total = (size_t)nf * nf * nf;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        int fx = (int)(t % nf);
-        int fy = (int)((t / nf) % nf);
-        int fz = (int)(t / ((size_t)nf * nf));
-        int ix = fx >> 1, iy = fy >> 1, iz = fz >> 1;
-        int jx = min(max(ix + ((fx & 1) ? 1 : -1), 0), nc - 1);
-        int jy = min(max(iy + ((fy & 1) ? 1 : -1), 0), nc - 1);
-        int jz = min(max(iz + ((fz & 1) ? 1 : -1), 0), nc - 1);
-        const int xs[2] = {ix, jx}, ys[2] = {iy, jy}, zs[2] = {iz, jz};
-        const float w[2] = {0.75f, 0.25f};
-        float acc = 0.0f;
+    const int i = blockIdx.x * 128 + threadIdx.x;
+    if (i >= nc) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int xs[3] = {max(i - 1, 0), i, min(i + 1, nc - 1)};
+    const int ys[3] = {max(j - 1, 0), j, min(j + 1, nc - 1)};
+    const int zs[3] = {max(k - 1, 0), k, min(k + 1, nc - 1)};
+    // the fine cells first, so that their loads overlap the coarse ones
+    float2 *f[2][2];
+    float2 fv[2][2];
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+    for (int pz = 0; pz < 2; ++pz)
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
+        for (int py = 0; py < 2; ++py) {
+            f[pz][py] = reinterpret_cast<float2 *>(fine + ((size_t)(2 * k + pz) * nf + (2 * j + py)) * nf) + i;
+            fv[pz][py] = *f[pz][py];
+        }
+    // along x: ex = fine 2i, ox = fine 2i + 1, per coarse (z, y) row
+    float ex[3][3], ox[3][3];
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    size_t ci = ((size_t)zs[a] * nc + ys[b]) * nc + xs[c];
-                    acc = fmaf(w[a] * w[b] * w[c], __ldg(cn + ci) - __ldg(co + ci), acc);
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const size_t row = ((size_t)zs[a] * nc + ys[b]) * nc;
+            const float dm = __ldg(cn + row + xs[0]) - __ldg(co + row + xs[0]);
+            const float d0 = __ldg(cn + row + xs[1]) - __ldg(co + row + xs[1]);
+            const float dp = __ldg(cn + row + xs[2]) - __ldg(co + row + xs[2]);
+            ex[a][b] = fmaf(0.75f, d0, 0.25f * dm);
+            ox[a][b] = fmaf(0.75f, d0, 0.25f * dp);
+        }
+    // along y, then z
+#pragma unroll
+    for (int pz = 0; pz < 2; ++pz)
+#pragma unroll
+        for (int py = 0; py < 2; ++py) {
+            float vx[2];
+#pragma unroll
+            for (int px = 0; px < 2; ++px) {
+                float yz[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float *r = px ? ox[a] : ex[a];
+                    yz[a] = fmaf(0.75f, r[1], 0.25f * r[py ? 2 : 0]);
                 }
-        fine[t] += acc;
-    }
+                vx[px] = fmaf(0.75f, yz[1], 0.25f * yz[pz ? 2 : 0]);
+            }
+            *f[pz][py] = make_float2(fv[pz][py].x + vx[0], fv[pz][py].y + vx[1]);
+        }
 }
 
 static int grid_for(size_t total, int threads = 256) {
@@ -252,8 +407,11 @@ int launch_restrict_sino(int k, int nv, int nu, const float *in, float *out, cud
 }
 
 int launch_prolong_add(int nc, const float *cn, const float *co, float *fine, cudaStream_t s) {
-    size_t nf = 2 * (size_t)nc;
-    MGCT_KERNEL(KK_GRID, s, k_prolong_add<<<grid_for(nf * nf * nf), 256, 0, s>>>(nc, cn, co, fine));
+    const int nf = 2 * nc;
+    if (nc < 1) return MGCT_OK;
+    (void)nf;
+    dim3 grid((nc + 127) / 128, nc, nc);
+    MGCT_KERNEL(KK_GRID, s, k_prolong_add<<<grid, 128, 0, s>>>(nc, cn, co, fine));
     return MGCT_OK;
 }
 

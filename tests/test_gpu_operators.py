@@ -237,11 +237,13 @@ def test_full_size_sampled(cfg):
 
 # --------------------------------------------------------------------------- p, R, P
 
-@pytest.mark.parametrize("axis", [2, 0])
-def test_precondition(axis):
-    d = scan_desc(40, 48, 48, 4, 1, levels=1, slice_axis=axis)
+@pytest.mark.parametrize("axis,n", [(2, 40), (2, 37), (2, 150), (0, 40), (1, 33)])
+def test_precondition(axis, n):
+    """Eq. 5 against the oracle: the z-slice stream kernel (vector and scalar
+    staging, partial tiles) and the generic stencil for the other axes."""
+    d = scan_desc(n, 48, 48, 4, 1, levels=1, slice_axis=axis)
     g = gpu_geom(d)
-    x = synth.random_volume(40, 18).astype(np.float32) - 0.5
+    x = synth.random_volume(n, 18).astype(np.float32) - 0.5
     ref = O.precondition(x.astype(np.float64), axis)
     got = to_np(mgct.precondition(g, cuda(x)))
     assert np.abs(got - ref).max() <= 1e-6 * np.abs(x).max()
@@ -254,12 +256,13 @@ def test_restrict_and_prolong():
     b = np.random.default_rng(20).random((5, 36, 52)).astype(np.float32)
     got = to_np(mgct.restrict_sino(cuda(b)))
     assert np.abs(got - O.restrict_sino(b.astype(np.float64))).max() <= 1e-6
-    cn = synth.random_volume(20, 21).astype(np.float32)
-    co = synth.random_volume(20, 22).astype(np.float32)
-    fine = synth.random_volume(40, 23).astype(np.float32)
-    ref = fine.astype(np.float64) + O.prolong(cn.astype(np.float64) - co.astype(np.float64))
-    got = to_np(mgct.prolong_add(cuda(cn), cuda(co), cuda(fine)))
-    assert np.abs(got - ref).max() <= 1e-6
+    for nc in (20, 131):  # one and two 128-wide blocks along x
+        cn = synth.random_volume(nc, 21).astype(np.float32)
+        co = synth.random_volume(nc, 22).astype(np.float32)
+        fine = synth.random_volume(2 * nc, 23).astype(np.float32)
+        ref = fine.astype(np.float64) + O.prolong(cn.astype(np.float64) - co.astype(np.float64))
+        got = to_np(mgct.prolong_add(cuda(cn), cuda(co), cuda(fine)))
+        assert np.abs(got - ref).max() <= 1e-6
 
 
 @pytest.mark.parametrize("cfg", [(256, 384, 720), (512, 768, 1440)], ids=["c2", "c3"])

@@ -372,6 +372,16 @@ const char *mgct_last_error(void);
 /* Kernel launches issued by this thread since the last reset (host counter). */
 uint64_t mgct_launch_count(int reset);
 
+/* Self-check of the failure path of the library's device waits (the paper
+ * has no counterpart).  Every wait in the library's kernels on another
+ * agent's progress (the tensor-core convolutions' waits for their MMAs) is
+ * bounded by the SM clock, about a second, after which the kernel reports
+ * the expiry (see mgct_net_check) instead of hanging.  This runs that same
+ * bounded wait for `seconds` (0 < seconds <= 10) on a barrier nothing ever
+ * completes, synchronises `stream`, and sets *expired = 1 when the wait gave
+ * up as designed.  Returns MGCT_OK (the device context stays usable). */
+int mgct_check_bounded_wait(double seconds, int *expired, mgct_stream stream);
+
 /* Kernel trace (tracing subsystem; the paper has none).  mgct_trace_enable(1)
  * clears the record and starts recording a CUDA event pair on the launching
  * stream around every kernel the library issues; 0 stops and clears.

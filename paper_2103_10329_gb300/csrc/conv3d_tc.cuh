@@ -51,11 +51,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
     return done != 0;
 }
 
-// Bounded wait for the completion of the phase with this parity.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity) {
-    for (int it = 0; it < (1 << 24); ++it)
-        if (mbar_try_wait(mbar, parity)) return true;
-    return false;
+// Bounded wait for the completion of the phase with this parity: gives up
+// after `limit` SM clock cycles (the default, 2^31, is about a second at
+// 2 GHz) and returns false, so that a block whose MMAs never complete reports
+// it instead of hanging.
+constexpr long long MBAR_WAIT_CYCLES = 1LL << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity,
+                                                  long long limit = MBAR_WAIT_CYCLES) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
 }
 
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {

@@ -123,6 +123,17 @@ def launch_count(reset: bool = False) -> int:
     return int(lib().mgct_launch_count(1 if reset else 0))
 
 
+def check_bounded_wait(seconds: float = 0.2) -> bool:
+    """Run the library's bounded device wait on a barrier nothing completes
+    (mgct_check_bounded_wait); True when it expired and reported as designed."""
+    L = lib()
+    L.mgct_check_bounded_wait.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    L.mgct_check_bounded_wait.restype = ctypes.c_int
+    flag = ctypes.c_int(0)
+    _check(L.mgct_check_bounded_wait(float(seconds), ctypes.byref(flag), _stream()))
+    return flag.value == 1
+
+
 TRACE_KINDS = ("project", "backproject", "precondition", "transpose", "grid", "update", "reduce",
                "geomgrad", "conv", "other")
 

@@ -59,3 +59,7 @@ def test_host_side_argument_checks(L):
     assert L.mgct_geometry_create(ctypes.byref(desc), ctypes.byref(h)) == -1
     assert L.mgct_workspace_bytes(None, 0, 0) == 0
     assert L.mgct_net_check(None, None) == -1
+    L.mgct_check_bounded_wait.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    flag = ctypes.c_int(0)
+    assert L.mgct_check_bounded_wait(0.0, ctypes.byref(flag), None) == -1
+    assert L.mgct_check_bounded_wait(0.1, None, None) == -1

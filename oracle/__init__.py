@@ -366,6 +366,34 @@ def soft_threshold(x: np.ndarray, lam: float) -> np.ndarray:
     return np.sign(x) * np.maximum(np.abs(x) - lam, 0.0)
 
 
+def bilateral_filter(x: np.ndarray, sigma_s: float, sigma_r: float, radius: int) -> np.ndarray:
+    """BilateralFilter of Alg. 1 (its parameters are not given in the paper):
+        out(p) = sum_q w(p, q) x(q) / sum_q w(p, q),
+        w(p, q) = exp(-|p - q|^2 / (2 sigma_s^2)) exp(-(x(p) - x(q))^2 / (2 sigma_r^2)),
+    q over the (2 radius + 1)^3 window around p that lies inside the volume
+    (distances in voxels of the grid)."""
+    x = np.asarray(x, dtype=np.float64)
+    n0, n1, n2 = x.shape
+    num = np.zeros_like(x)
+    den = np.zeros_like(x)
+    for dz in range(-radius, radius + 1):
+        for dy in range(-radius, radius + 1):
+            for dx in range(-radius, radius + 1):
+                ws = np.exp(-(dz * dz + dy * dy + dx * dx) / (2.0 * sigma_s * sigma_s))
+                # q = p + (dz, dy, dx): the part of the volume where q is inside
+                zs, ze = max(0, -dz), min(n0, n0 - dz)
+                ys, ye = max(0, -dy), min(n1, n1 - dy)
+                xs, xe = max(0, -dx), min(n2, n2 - dx)
+                if zs >= ze or ys >= ye or xs >= xe:
+                    continue
+                xp = x[zs:ze, ys:ye, xs:xe]
+                xq = x[zs + dz:ze + dz, ys + dy:ye + dy, xs + dx:xe + dx]
+                w = ws * np.exp(-((xp - xq) ** 2) / (2.0 * sigma_r * sigma_r))
+                num[zs:ze, ys:ye, xs:xe] += w * xq
+                den[zs:ze, ys:ye, xs:xe] += w
+    return num / den
+
+
 # ----------------------------------------------------------------------------
 # Grid transfer (Alg. 1 Restrict / Prolongate)
 # ----------------------------------------------------------------------------
@@ -461,7 +489,7 @@ def data_levels(b: np.ndarray, levels: int):
 def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
               lam: float = 0.0, n_subsets: int = 8, alpha: float | None = None,
               precond: bool = True, stats: list | None = None, fas: bool = False,
-              b: np.ndarray | None = None) -> np.ndarray:
+              b: np.ndarray | None = None, bilateral: tuple | None = None) -> np.ndarray:
     """Alg. 1 on grid `level`; returns the updated estimate on that grid.
 
     The coarse problem's data is the restricted radiographs R b (Alg. 1).
@@ -472,7 +500,9 @@ def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
     exact solution of the fine problem is a fixed point of the iteration.
     parity unpinned beyond L = 1 for the plain recursion (no closed form):
     checked against the paper's qualitative claim and against the GPU; the FAS
-    form is pinned by its fixed point."""
+    form is pinned by its fixed point.  bilateral = (sigma_s, sigma_r, radius)
+    applies Alg. 1's BilateralFilter after each grid's Landweber step and soft
+    threshold (None: not applied)."""
     g = level_geometry(scan, level)
     mu = np.asarray(mu, dtype=np.float64)
     b_here = b_levels[level] if b is None else np.asarray(b, dtype=np.float64)
@@ -484,12 +514,14 @@ def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
             b_c = b_levels[level + 1]
         if level + 1 < levels - 1:
             mu_c_new = multigrid(scan, mu_c, b_levels, levels, level + 1, lam, n_subsets,
-                                 alpha, precond, stats, fas=fas, b=b_c)
+                                 alpha, precond, stats, fas=fas, b=b_c, bilateral=bilateral)
         else:
             mu_c_new = osemtr_pass(level_geometry(scan, level + 1), mu_c, b_c, n_subsets)
         mu = mu + prolong(mu_c_new - mu_c)
     mu, st = landweber_step(g, mu, b_here, alpha=alpha, lam=lam, precond=precond,
                             slice_axis=scan.slice_axis)
+    if bilateral is not None:
+        mu = bilateral_filter(mu, *bilateral)
     if stats is not None:
         st["level"] = level
         stats.append(st)
@@ -498,13 +530,13 @@ def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
 
 def reconstruct(scan: Scan, b: np.ndarray, iters: int = 2, levels: int = 2, lam: float = 0.0,
                 n_subsets: int = 8, mu0: np.ndarray | None = None, stats: list | None = None,
-                fas: bool = False):
+                fas: bool = False, bilateral: tuple | None = None):
     """`iters` multigrid iterations at grid 0 from mu = 0 (Fig. 3: one or two);
     fas=True takes the FAS coarse data (see multigrid)."""
     bl = data_levels(b, levels)
     mu = np.zeros((scan.n,) * 3) if mu0 is None else np.asarray(mu0, dtype=np.float64)
     for _ in range(iters):
-        mu = multigrid(scan, mu, bl, levels, 0, lam, n_subsets, stats=stats, fas=fas)
+        mu = multigrid(scan, mu, bl, levels, 0, lam, n_subsets, stats=stats, fas=fas, bilateral=bilateral)
     return mu
 
 

@@ -422,6 +422,55 @@ def test_multigrid_structure_two_levels():
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
 
 
+# ---------------------------------------------------------------- bilateral filter (Alg. 1)
+
+def test_bilateral_brute_force():
+    """The definition, voxel by voxel, on a tiny volume (window clipped at the
+    faces)."""
+    x = synth.random_volume(5, 40)
+    ss, sr, r = 0.9, 0.3, 1
+    got = O.bilateral_filter(x, ss, sr, r)
+    for p in [(0, 0, 0), (2, 3, 1), (4, 4, 4), (1, 0, 3)]:
+        num = den = 0.0
+        for q in np.ndindex(5, 5, 5):
+            d = np.subtract(q, p)
+            if np.abs(d).max() > r:
+                continue
+            w = math.exp(-float(d @ d) / (2 * ss * ss)) * math.exp(-(x[p] - x[q]) ** 2 / (2 * sr * sr))
+            num += w * x[q]
+            den += w
+        assert math.isclose(got[p], num / den, rel_tol=1e-13)
+
+
+def test_bilateral_limits():
+    """A huge range sigma leaves the normalised Gaussian: in the interior it is
+    scipy's correlation with the normalised kernel; a tiny one leaves the
+    identity (no two random values are equal); constants are kept."""
+    x = synth.random_volume(12, 41)
+    g = np.array([[[math.exp(-((a - 2) ** 2 + (b - 2) ** 2 + (c - 2) ** 2) / (2 * 1.3 ** 2)) for c in range(5)]
+                   for b in range(5)] for a in range(5)])
+    g /= g.sum()
+    wide = O.bilateral_filter(x, 1.3, 1e9, 2)
+    ref = scipy.ndimage.correlate(x, g, mode="constant")
+    np.testing.assert_allclose(wide[2:-2, 2:-2, 2:-2], ref[2:-2, 2:-2, 2:-2], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(O.bilateral_filter(x, 1.0, 1e-6, 1), x, rtol=0, atol=1e-12)
+    c = np.full((6, 6, 6), 0.37)
+    np.testing.assert_allclose(O.bilateral_filter(c, 1.0, 0.1, 2), c, rtol=1e-14)
+
+
+def test_multigrid_bilateral_is_applied_after_each_landweber_step():
+    """Alg. 1 order at one grid: Landweber step (with its soft threshold), then
+    the bilateral filter."""
+    n = 8
+    scan = make_scan(n, nviews=6, seed=14)
+    g = O.level_geometry(scan, 0)
+    b = O.project(g, synth.random_volume(n, 15))
+    mu0 = 0.1 * synth.random_volume(n, 16)
+    got = O.multigrid(scan, mu0, [b], levels=1, lam=0.01, bilateral=(1.0, 0.2, 1))
+    lw, _ = O.landweber_step(g, mu0, b, lam=0.01)
+    np.testing.assert_allclose(got, O.bilateral_filter(lw, 1.0, 0.2, 1), rtol=0, atol=1e-13)
+
+
 def _fas_case(n=16, nviews=40, levels=2):
     scan = make_scan(n, nviews=nviews, seed=21)
     ph = synth.ellipsoids(6, 3, axis_lo=0.08, axis_hi=0.3)

@@ -602,7 +602,7 @@ def gpu_arm(args, rank, world):
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
 
-        def run_iters(storage, iters, net=None):
+        def run_iters(storage, iters, net=None, bilateral=None):
             v = torch.zeros_like(vol)
             out = []
             tot = 0.0
@@ -610,7 +610,7 @@ def gpu_arm(args, rank, world):
                 torch.cuda.synchronize()
                 s0.record()
                 if net is None:
-                    rec.iterate(v, storage=storage)
+                    rec.iterate(v, storage=storage, bilateral=bilateral)
                 else:
                     rec.iterate_learned(v, net, storage=storage)
                 s1.record()
@@ -641,8 +641,18 @@ def gpu_arm(args, rank, world):
         forms = [("fp32", torch.float32, False), ("bf16", torch.bfloat16, False), ("fp16", torch.float16, False)]
         if net is not None:
             forms += [("learned_fp32", torch.float32, True), ("learned_bf16", torch.bfloat16, True)]
+        # Alg. 1's BilateralFilter (no parameters in the paper): sigma_s = 1 voxel,
+        # sigma_r = 0.2, radius 1, the best of five settings tried on this workload
+        bil = (1.0, 0.2, 1)
+        forms += [("bilateral_fp32", torch.float32, "bil"), ("bilateral_bf16", torch.bfloat16, "bil")]
+        tta["bilateral"] = {"sigma_s_voxels": bil[0], "sigma_r": bil[1], "radius": bil[2],
+                            "chosen": "best of (1, 0.05, 1), (1, 0.1, 1), (1, 0.2, 1), (1.5, 0.1, 2), (0.8, 0.1, 1) "
+                                      "on this workload; E2 stays the plain form's"}
         for name, st, use_net in forms:
-            hist = run_iters(st, 3, net if use_net else None)
+            if use_net == "bil":
+                hist = run_iters(st, 3, None, bil)
+            else:
+                hist = run_iters(st, 3, net if use_net else None)
             reach = next(((i + 1, t) for i, (t, e) in enumerate(hist) if e <= e2 * (1 + 1e-3)), None)
             tta["forms"][name] = {"per_iter_ms_cum": [h[0] for h in hist], "per_iter_rmse_roi": [h[1] for h in hist],
                                   "iters_to_E2": reach[0] if reach else None,

@@ -193,6 +193,13 @@ typedef struct {
                              solution becomes a fixed point, removing the plateau of the
                              plain recursion on consistent data */
     const float *learned_corr; /* reserved, must be NULL */
+    /* Alg. 1 BilateralFilter after each grid's Landweber step and soft threshold
+     * in the multigrid recursion (mgct_multigrid_iteration / _coarse; see
+     * mgct_bilateral).  The paper gives no parameters: radius 0 = off. */
+    double bilateral_sigma_s;  /* spatial sigma, voxels of the grid (> 0 when on) */
+    double bilateral_sigma_r;  /* range sigma, attenuation units (> 0 when on) */
+    int32_t bilateral_radius;  /* window half-width, 0 (off) .. 4 */
+    int32_t reserved1;         /* must be 0 */
 } mgct_lw_opts;
 
 /* Device-side record of one Landweber step (float64). */
@@ -222,6 +229,15 @@ int mgct_landweber_step(const mgct_geom *geom, int level, float *vol, const floa
 int mgct_osemtr_pass(const mgct_geom *geom, int level, int n_subsets, float *vol,
                      const float *b, const float *pi, void *workspace, size_t ws_bytes,
                      mgct_stream stream);
+
+/* Alg. 1 BilateralFilter (its parameters are not given in the paper):
+ *   out(p) = sum_q w(p,q) in(q) / sum_q w(p,q),
+ *   w(p,q) = exp(-|p-q|^2 / (2 sigma_s^2)) exp(-(in(p)-in(q))^2 / (2 sigma_r^2)),
+ * q over the (2 radius + 1)^3 window around p inside the volume, distances in
+ * voxels.  in, out: float32 [n]^3, distinct (out-of-place).  sigma_s > 0,
+ * sigma_r > 0, 1 <= radius <= 4. */
+int mgct_bilateral(int n, const float *in, float *out, double sigma_s, double sigma_r, int radius,
+                   mgct_stream stream);
 
 /* Alg. 1.  mgct_multigrid_prepare stores b on every grid (2x2 restriction)
  * and PI = A 1 on the coarsest grid in the workspace; then each

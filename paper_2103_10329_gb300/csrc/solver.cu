@@ -26,6 +26,8 @@ int launch_scaled_copy(size_t count, const float *d, const double *alpha, float 
 int launch_update_choice(size_t count, float *mu, const float *d, const float *dl, const double *st, float lam,
                          cudaStream_t s);
 int launch_axpy(size_t count, float a, const float *x, float *y, cudaStream_t s);
+int launch_bilateral(int n, const float *in, float *out, double sigma_s, double sigma_r, int radius, cudaStream_t s);
+
 int launch_column_table_df(const mgct_geom *g, int level, cudaStream_t s) {
     const LevelInfo &L = g->lev[level];
     const int K = g->desc.n_views;
@@ -344,7 +346,17 @@ static int multigrid_level(const mgct_geom *g, int level, float *mu, const MGSpa
         MGCT_TRY(launch_prolong_add(C.n, mc, oc, mu, s));
     }
     if (skip_landweber) return MGCT_OK;
-    return landweber(g, level, mu, b, m.lw_base, o, stats ? stats + level : nullptr, s);
+    MGCT_TRY(landweber(g, level, mu, b, m.lw_base, o, stats ? stats + level : nullptr, s));
+    if (o.bilateral_radius > 0) {
+        // Alg. 1 BilateralFilter; the Landweber workspace's gradient volume is free now
+        Carver cw(m.lw_base);
+        LWSpace w = carve_lw(g, 0, cw);
+        const int n = g->lev[level].n;
+        MGCT_TRY(launch_bilateral(n, mu, w.grad, o.bilateral_sigma_s, o.bilateral_sigma_r, o.bilateral_radius, s));
+        MGCT_TRY(check_cuda(cudaMemcpyAsync(mu, w.grad, vox(g->lev[level]) * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                            "copy filtered volume"));
+    }
+    return MGCT_OK;
 }
 
 static int check_opts(const mgct_lw_opts *o) {
@@ -355,6 +367,10 @@ static int check_opts(const mgct_lw_opts *o) {
     if (o->storage < MGCT_F32 || o->storage > MGCT_F16)
         return set_error(MGCT_EINVAL, "storage must be MGCT_F32, MGCT_BF16 or MGCT_F16");
     if (o->coarse_fas != 0 && o->coarse_fas != 1) return set_error(MGCT_EINVAL, "coarse_fas must be 0 or 1");
+    if (o->reserved1 != 0) return set_error(MGCT_EINVAL, "reserved1 must be 0");
+    if (o->bilateral_radius < 0 || o->bilateral_radius > 4) return set_error(MGCT_EINVAL, "bilateral_radius must be 0..4");
+    if (o->bilateral_radius > 0 && !(o->bilateral_sigma_s > 0.0 && o->bilateral_sigma_r > 0.0))
+        return set_error(MGCT_EINVAL, "bilateral sigmas must be > 0");
     return MGCT_OK;
 }
 
@@ -500,6 +516,16 @@ int mgct_osemtr_pass(const mgct_geom *g, int level, int n_subsets, float *vol, c
     MGCT_TRY(check_ptr(pi, "pi"));
     MGCT_TRY(check_ws(g, MGCT_WS_OSEMTR, level, ws, bytes));
     return osemtr(g, level, n_subsets, vol, b, pi, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgct_bilateral(int n, const float *in, float *out, double sigma_s, double sigma_r, int radius, mgct_stream stream) {
+    if (n < 1) return set_error(MGCT_ESHAPE, "n must be >= 1");
+    MGCT_TRY(check_ptr(in, "in"));
+    MGCT_TRY(check_ptr(out, "out"));
+    if (in == out) return set_error(MGCT_EINVAL, "in and out must differ");
+    if (radius < 1 || radius > 4) return set_error(MGCT_EINVAL, "radius must be 1..4");
+    if (!(sigma_s > 0.0 && sigma_r > 0.0)) return set_error(MGCT_EINVAL, "sigmas must be > 0");
+    return launch_bilateral(n, in, out, sigma_s, sigma_r, radius, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int mgct_multigrid_prepare(const mgct_geom *g, const float *b, void *ws, size_t bytes, mgct_stream stream) {

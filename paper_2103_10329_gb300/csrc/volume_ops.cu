@@ -416,6 +416,47 @@ int launch_prolong_add(int nc, const float *cn, const float *co, float *fine, cu
 }
 
 // ---------------------------------------------------------------------------
+// Alg. 1 BilateralFilter: out(p) = sum_q w x(q) / sum_q w over the window
+// |q - p|_inf <= r inside the volume, w = exp(-|q - p|^2 / 2 ss^2 -
+// (x(q) - x(p))^2 / 2 sr^2) (one __expf per neighbour; the self weight is 1).
+// Thread = voxel; the window's values come through L1.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bilateral(int n, const float *__restrict__ in, float *__restrict__ out,
+                                                   float inv2ss, float inv2sr, int r) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    if (x >= n || y >= n) return;
+    const size_t nn = (size_t)n * n;
+    const float c = __ldg(in + z * nn + (size_t)y * n + x);
+    float num = 0.0f, den = 0.0f;
+    for (int dz = -r; dz <= r; ++dz) {
+        const int zz = z + dz;
+        if ((unsigned)zz >= (unsigned)n) continue;
+        for (int dy = -r; dy <= r; ++dy) {
+            const int yy = y + dy;
+            if ((unsigned)yy >= (unsigned)n) continue;
+            const float *row = in + zz * nn + (size_t)yy * n;
+            const float dzy = (float)(dz * dz + dy * dy);
+            for (int dx = -r; dx <= r; ++dx) {
+                const int xx = x + dx;
+                if ((unsigned)xx >= (unsigned)n) continue;
+                const float v = __ldg(row + xx), d = v - c;
+                const float w = __expf(-(dzy + (float)(dx * dx)) * inv2ss - d * d * inv2sr);
+                num = fmaf(w, v, num);
+                den += w;
+            }
+        }
+    }
+    out[z * nn + (size_t)y * n + x] = num / den;
+}
+
+int launch_bilateral(int n, const float *in, float *out, double sigma_s, double sigma_r, int radius, cudaStream_t s) {
+    dim3 grid((n + 31) / 32, (n + 7) / 8, n);
+    MGCT_KERNEL(KK_UPDATE, s, k_bilateral<<<grid, dim3(32, 8), 0, s>>>(n, in, out, (float)(0.5 / (sigma_s * sigma_s)),
+                                                                         (float)(0.5 / (sigma_r * sigma_r)), radius));
+    return MGCT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic float64 reductions: one block sums the partials in a fixed
 // order (strided per thread, then a fixed tree).
 // ---------------------------------------------------------------------------

@@ -37,7 +37,9 @@ class LwOpts(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("precondition", ctypes.c_int32), ("n_subsets", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("coarse_fas", ctypes.c_int32),
-                ("learned_corr", ctypes.c_void_p)]
+                ("learned_corr", ctypes.c_void_p),
+                ("bilateral_sigma_s", ctypes.c_double), ("bilateral_sigma_r", ctypes.c_double),
+                ("bilateral_radius", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 _lib = None
@@ -297,9 +299,10 @@ def workspace(geom: Geometry, op: int, level: int = 0, device="cuda") -> torch.T
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
-def _opts(alpha, lam, precond, n_subsets, storage=torch.float32, fas=False):
+def _opts(alpha, lam, precond, n_subsets, storage=torch.float32, fas=False, bilateral=None):
+    ss, sr, r = bilateral if bilateral is not None else (0.0, 0.0, 0)
     return LwOpts(float(alpha) if alpha is not None else 0.0, float(lam), 1 if precond else 0,
-                  int(n_subsets), _DT[storage], 1 if fas else 0, None)
+                  int(n_subsets), _DT[storage], 1 if fas else 0, None, float(ss), float(sr), int(r), 0)
 
 
 def landweber_step(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, level: int = 0, alpha=None,
@@ -334,10 +337,13 @@ def multigrid_prepare(geom: Geometry, b: torch.Tensor, ws: torch.Tensor):
 
 def multigrid_iteration(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, ws: torch.Tensor, alpha=None,
                         lam: float = 0.0, precond: bool = True, n_subsets: int = 8,
-                        stats: torch.Tensor | None = None, storage=torch.float32, fas: bool = False):
+                        stats: torch.Tensor | None = None, storage=torch.float32, fas: bool = False,
+                        bilateral=None):
     """One Alg. 1 iteration at grid 0; fas=True takes the full-approximation-
-    scheme coarse data R(b - A mu) + A_c(R mu) (a variant outside the paper)."""
-    o = _opts(alpha, lam, precond, n_subsets, storage, fas)
+    scheme coarse data R(b - A mu) + A_c(R mu) (a variant outside the paper);
+    bilateral = (sigma_s, sigma_r, radius) applies Alg. 1's BilateralFilter
+    after each grid's Landweber step."""
+    o = _opts(alpha, lam, precond, n_subsets, storage, fas, bilateral)
     _check(lib().mgct_multigrid_iteration(geom.handle, _ptr(vol, "vol", torch.float32),
                                           _ptr(b, "b", torch.float32), _ptr(ws, "ws"), ws.numel(),
                                           ctypes.byref(o), _ptr(stats, "stats", torch.float64), _stream()))
@@ -346,10 +352,10 @@ def multigrid_iteration(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, ws: 
 
 def multigrid_coarse(geom: Geometry, vol: torch.Tensor, ws: torch.Tensor, n_subsets: int = 8,
                      stats: torch.Tensor | None = None, storage=torch.float32, lam: float = 0.0,
-                     b: torch.Tensor | None = None, fas: bool = False):
+                     b: torch.Tensor | None = None, fas: bool = False, bilateral=None):
     """Alg. 1 without the grid-0 Landweber step; b (grid-0 data) is needed
     with fas=True."""
-    o = _opts(None, lam, True, n_subsets, storage, fas)
+    o = _opts(None, lam, True, n_subsets, storage, fas, bilateral)
     _check(lib().mgct_multigrid_coarse(geom.handle, _ptr(vol, "vol", torch.float32), _ptr(b, "b", torch.float32),
                                        _ptr(ws, "ws"), ws.numel(), ctypes.byref(o),
                                        _ptr(stats, "stats", torch.float64), _stream()))
@@ -387,6 +393,20 @@ def landweber_learned(geom: Geometry, vol: torch.Tensor, b: torch.Tensor, net: "
                                         net.handle, _ptr(nws, "net_ws"), nws.numel(),
                                         _ptr(stats, "stats", torch.float64), _stream()))
     return vol
+
+
+def bilateral(x: torch.Tensor, sigma_s: float, sigma_r: float, radius: int, out: torch.Tensor | None = None):
+    """Alg. 1 BilateralFilter of a float32 [n]^3 volume (mgct_bilateral)."""
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty_like(x)
+    L = lib()
+    L.mgct_bilateral.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_void_p]
+    L.mgct_bilateral.restype = ctypes.c_int
+    _check(L.mgct_bilateral(n, _ptr(x, "x", torch.float32), _ptr(out, "out", torch.float32), float(sigma_s),
+                            float(sigma_r), int(radius), _stream()))
+    return out
 
 
 def axpy(a: float, x: torch.Tensor, y: torch.Tensor):

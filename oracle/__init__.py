@@ -109,6 +109,7 @@ class Scan:
     src_det_dist: float = 4.0   # L: source to detector
     drift: np.ndarray | None = None  # [K, 5] (ds_u, ds_v, dd_u, dd_v [pixels], psi [rad])
     slice_axis: int = 2         # Eq. 5 outer index: 2 = z, 0 = x
+    p_kernel: np.ndarray | None = None  # [3][3][3] preconditioner replacing Eq. 5 (correlation), or None
     extra: dict = field(default_factory=dict)
 
     @property
@@ -345,10 +346,12 @@ def eq5_kernel(slice_axis: int = 2) -> np.ndarray:
     raise ValueError(slice_axis)
 
 
-def precondition(x: np.ndarray, slice_axis: int = 2) -> np.ndarray:
-    """p * x (Eq. 4 and 5): 27-point convolution, zero outside the volume.
-    The kernel is symmetric, so convolution and correlation coincide."""
-    k = eq5_kernel(slice_axis)
+def precondition(x: np.ndarray, slice_axis: int = 2, kernel: np.ndarray | None = None) -> np.ndarray:
+    """p * x (Eq. 4 and 5): 27-point correlation out(p) = sum_d k[d] x(p + d),
+    d in {-1, 0, 1}^3 indexed [dz][dy][dx], zero outside the volume.  Eq. 5
+    is symmetric, so convolution and correlation coincide for it; `kernel`
+    (a [3][3][3] array) replaces it."""
+    k = eq5_kernel(slice_axis) if kernel is None else np.asarray(kernel, dtype=np.float64).reshape(3, 3, 3)
     n0, n1, n2 = x.shape
     pad = np.zeros((n0 + 2, n1 + 2, n2 + 2))
     pad[1:-1, 1:-1, 1:-1] = x
@@ -434,14 +437,15 @@ def prolong(c: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 
 def landweber_step(g: LevelGeom, mu: np.ndarray, b: np.ndarray, alpha: float | None = None,
-                   lam: float = 0.0, precond: bool = True, slice_axis: int = 2):
+                   lam: float = 0.0, precond: bool = True, slice_axis: int = 2,
+                   kernel: np.ndarray | None = None):
     """One preconditioned Landweber step (Eq. 4; Eq. 2 when precond=False):
     mu <- S_lambda(mu + alpha p * B(b - P mu)).  alpha=None takes the exact
     line search alpha = <r, A d> / |A d|^2 (0 when A d = 0).
     Returns (mu_new, stats)."""
     r = b - project(g, mu)
     grad = backproject(g, r)
-    d = precondition(grad, slice_axis) if precond else grad
+    d = precondition(grad, slice_axis, kernel) if precond else grad
     ad = None
     if alpha is None:
         ad = project(g, d)
@@ -519,7 +523,7 @@ def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
             mu_c_new = osemtr_pass(level_geometry(scan, level + 1), mu_c, b_c, n_subsets)
         mu = mu + prolong(mu_c_new - mu_c)
     mu, st = landweber_step(g, mu, b_here, alpha=alpha, lam=lam, precond=precond,
-                            slice_axis=scan.slice_axis)
+                            slice_axis=scan.slice_axis, kernel=scan.p_kernel)
     if bilateral is not None:
         mu = bilateral_filter(mu, *bilateral)
     if stats is not None:

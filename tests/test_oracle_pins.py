@@ -422,6 +422,17 @@ def test_multigrid_structure_two_levels():
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
 
 
+def test_precondition_custom_kernel():
+    """A kernel given in place of Eq. 5 is applied as the correlation
+    out(p) = sum_d k[d] x(p + d) (scipy's `correlate`, zero padding); Eq. 5
+    itself passed as the kernel reproduces the default."""
+    x = synth.random_volume(9, 60) - 0.5
+    k = np.random.default_rng(61).standard_normal((3, 3, 3))
+    np.testing.assert_allclose(O.precondition(x, kernel=k), scipy.ndimage.correlate(x, k, mode="constant"),
+                               rtol=0, atol=1e-13)
+    np.testing.assert_allclose(O.precondition(x, kernel=O.eq5_kernel(2)), O.precondition(x), rtol=0, atol=0)
+
+
 # ---------------------------------------------------------------- bilateral filter (Alg. 1)
 
 def test_bilateral_brute_force():

@@ -632,6 +632,25 @@ def gpu_arm(args, rank, world):
                "E2_pmgl_fp32_2iter": e2, "pmgl_fp32_2iter_ms": base[-1][0],
                "sirt_2iter_ms": s0.elapsed_time(s1), "sirt_2iter_rmse_roi": roi_rmse(vs, truth),
                "forms": {}}
+        # Fig. 2 analogue: OS-EMTR (Eq. 3, M = 8 subsets) at full resolution
+        del vs
+        ones = torch.ones_like(vol)
+        pi = mgct.project(g, ones)
+        del ones
+        we = mgct.workspace(g, mgct.WS_OSEMTR, 0)
+        ve = torch.zeros_like(vol)
+        em, tot = [], 0.0
+        for _ in range(10):
+            torch.cuda.synchronize()
+            s0.record()
+            mgct.osemtr_pass(g, ve, b, pi, n_subsets=8, ws=we)
+            s1.record()
+            torch.cuda.synchronize()
+            tot += s0.elapsed_time(s1)
+            em.append((tot, roi_rmse(ve, truth)))
+        tta["osemtr_full_res"] = {"subsets": 8, "per_pass_ms_cum": [e[0] for e in em],
+                                  "per_pass_rmse_roi": [e[1] for e in em]}
+        del ve, we, pi
         net = None
         if not args.no_learned:
             t0 = time.perf_counter()
@@ -648,6 +667,23 @@ def gpu_arm(args, rank, world):
         tta["bilateral"] = {"sigma_s_voxels": bil[0], "sigma_r": bil[1], "radius": bil[2],
                             "chosen": "best of (1, 0.05, 1), (1, 0.1, 1), (1, 0.2, 1), (1.5, 0.1, 2), (0.8, 0.1, 1) "
                                       "on this workload; E2 stays the plain form's"}
+        # a preconditioner fitted to the measured PSF of A^T A (in place of Eq. 5)
+        from paper_2103_10329_gb300 import psf as PSF
+        t0 = time.perf_counter()
+        kern, _ = PSF.derived_preconditioner(g)
+        torch.cuda.synchronize()
+        fit_s = time.perf_counter() - t0
+        g.set_preconditioner(kern)
+        hist_psf = run_iters(torch.float32, 3)
+        g.set_preconditioner(None)
+        reach = next(((i + 1, t) for i, (t, e) in enumerate(hist_psf) if e <= e2 * (1 + 1e-3)), None)
+        tta["forms"]["psf_kernel_fp32"] = {"per_iter_ms_cum": [h[0] for h in hist_psf],
+                                           "per_iter_rmse_roi": [h[1] for h in hist_psf],
+                                           "iters_to_E2": reach[0] if reach else None,
+                                           "ms_to_E2": reach[1] if reach else None}
+        tta["psf_kernel"] = {"kernel_z0_plane": kern[1].tolist(), "kernel_z1_plane": kern[2].tolist(),
+                             "measure_and_fit_s": fit_s,
+                             "per_iter_ms_cum": [h[0] for h in hist_psf], "per_iter_rmse_roi": [h[1] for h in hist_psf]}
         for name, st, use_net in forms:
             if use_net == "bil":
                 hist = run_iters(st, 3, None, bil)

@@ -105,6 +105,13 @@ int mgct_geometry_create(const mgct_geom_desc *desc, mgct_geom **out);
 
 /* Replaces the drift of every view (host [K*5], or NULL for none) and
  * re-uploads the tables.  Synchronises the current device. */
+/* Preconditioner in place of Eq. 5 for mgct_precondition and the Landweber
+ * steps on every grid (the paper asks for better kernels than Eq. 5, Sec. 3):
+ * kernel = 27 doubles [dz][dy][dx], dz, dy, dx in {-1, 0, 1}, applied as the
+ * correlation out(p) = sum_d kernel[d] in(p + d) with zero padding (the
+ * slice-axis option does not apply to it).  NULL restores Eq. 5.  Not
+ * concurrent with calls that use the handle. */
+int mgct_geometry_set_preconditioner(mgct_geom *geom, const double *kernel);
 int mgct_geometry_set_drift(mgct_geom *geom, const double *drift);
 
 /* Frees the handle and its device memory.  NULL is ignored. */

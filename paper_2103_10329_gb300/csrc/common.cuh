@@ -94,6 +94,9 @@ struct mgct_geom {
     double *d_scratch_part;     // reduction partials
     size_t scratch_part_count;
     int device;
+    // preconditioner replacing Eq. 5 (mgct_geometry_set_preconditioner), [dz][dy][dx]
+    float pkernel[27];
+    int has_pkernel;
 };
 
 namespace mgct {

@@ -335,6 +335,19 @@ int mgct_geometry_create(const mgct_geom_desc *d, mgct_geom **out) {
     return MGCT_OK;
 }
 
+int mgct_geometry_set_preconditioner(mgct_geom *g, const double *kernel) {
+    if (!g) return set_error(MGCT_EINVAL, "geometry handle is NULL");
+    if (!kernel) {
+        g->has_pkernel = 0;
+        return MGCT_OK;
+    }
+    for (int i = 0; i < 27; ++i)
+        if (!std::isfinite(kernel[i])) return set_error(MGCT_EINVAL, "kernel coefficients must be finite");
+    for (int i = 0; i < 27; ++i) g->pkernel[i] = (float)kernel[i];
+    g->has_pkernel = 1;
+    return MGCT_OK;
+}
+
 int mgct_geometry_set_drift(mgct_geom *g, const double *drift) {
     if (!g) return set_error(MGCT_EINVAL, "geometry handle is NULL");
     int K = g->desc.n_views;

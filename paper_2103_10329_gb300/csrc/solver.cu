@@ -13,7 +13,7 @@
 
 namespace mgct {
 
-int launch_precondition(int n, int slice_axis, const float *in, float *out, cudaStream_t s);
+int launch_precondition(int n, int slice_axis, const float *in, float *out, cudaStream_t s, const float *custom);
 int launch_restrict_volume(int n_fine, const float *in, float *out, cudaStream_t s);
 int launch_restrict_sino(int k, int nv, int nu, const float *in, float *out, cudaStream_t s);
 int launch_prolong_add(int nc, const float *cn, const float *co, float *fine, cudaStream_t s);
@@ -196,7 +196,7 @@ static int lw_direction(const mgct_geom *g, int level, const float *mu, const fl
     MGCT_TRY(launch_backproject<1, ST, true>(g, level, 0, K, 1, r, w.grad, 0, s));
     *d_out = w.grad;
     if (o.precondition) {
-        MGCT_TRY(launch_precondition(L.n, g->desc.p_slice_axis, w.grad, w.d, s));
+        MGCT_TRY(launch_precondition(L.n, g->desc.p_slice_axis, w.grad, w.d, s, g->has_pkernel ? g->pkernel : nullptr));
         *d_out = w.d;
     }
     return MGCT_OK;
@@ -465,7 +465,8 @@ int mgct_precondition(const mgct_geom *g, int level, const float *in, float *out
     MGCT_TRY(check_ptr(in, "in"));
     MGCT_TRY(check_ptr(out, "out"));
     if (in == out) return set_error(MGCT_EINVAL, "in and out must not overlap");
-    return launch_precondition(g->lev[level].n, g->desc.p_slice_axis, in, out, reinterpret_cast<cudaStream_t>(stream));
+    return launch_precondition(g->lev[level].n, g->desc.p_slice_axis, in, out, reinterpret_cast<cudaStream_t>(stream),
+                               g->has_pkernel ? g->pkernel : nullptr);
 }
 
 int mgct_restrict_volume(int n_fine, const float *in, float *out, mgct_stream stream) {

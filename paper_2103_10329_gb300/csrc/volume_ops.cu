@@ -283,7 +283,14 @@ __global__ void __launch_bounds__(PZ_TX / 4 * PZ_TY) k_precondition_z(int n, con
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-int launch_precondition(int n, int slice_axis, const float *in, float *out, cudaStream_t s) {
+int launch_precondition(int n, int slice_axis, const float *in, float *out, cudaStream_t s, const float *custom) {
+    if (custom) {
+        Stencil27 K;
+        for (int i = 0; i < 27; ++i) K.c[i] = custom[i];
+        dim3 grid((n + ST_BX - 1) / ST_BX, (n + ST_BY - 1) / ST_BY, (n + ST_ZB - 1) / ST_ZB);
+        MGCT_KERNEL(KK_PRECONDITION, s, k_precondition_generic<<<grid, dim3(ST_BX, ST_BY), 0, s>>>(n, K, in, out));
+        return MGCT_OK;
+    }
     if (slice_axis == 2) {
         dim3 grid((n + PZ_TX - 1) / PZ_TX, (n + PZ_TY - 1) / PZ_TY, (n + PZ_ZB - 1) / PZ_ZB);
         MGCT_KERNEL(KK_PRECONDITION, s, k_precondition_z<<<grid, PZ_TX / 4 * PZ_TY, 0, s>>>(n, in, out));

@@ -185,6 +185,18 @@ class Geometry:
         _check(lib().mgct_geometry_set_drift(
             self.handle, None if self._drift is None else ctypes.c_void_p(self._drift.ctypes.data)))
 
+    def set_preconditioner(self, kernel=None):
+        """A [3][3][3] kernel ([dz][dy][dx], applied as a correlation) in place
+        of Eq. 5 on every grid; None restores Eq. 5."""
+        L = lib()
+        L.mgct_geometry_set_preconditioner.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.mgct_geometry_set_preconditioner.restype = ctypes.c_int
+        if kernel is None:
+            _check(L.mgct_geometry_set_preconditioner(self.handle, None))
+            return
+        k = np.ascontiguousarray(kernel, dtype=np.float64).reshape(27)
+        _check(L.mgct_geometry_set_preconditioner(self.handle, ctypes.c_void_p(k.ctypes.data)))
+
     def level(self, g: int):
         n, nu, nv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         h, p = ctypes.c_double(), ctypes.c_double()

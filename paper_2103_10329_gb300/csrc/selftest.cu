@@ -9,7 +9,9 @@
 
 namespace mgct {
 
-__global__ void k_wait_expires(long long limit, int *expired) {
+__device__ int g_wait_expired;  // the self-check's result (no allocation)
+
+__global__ void k_wait_expires(long long limit) {
     __shared__ __align__(8) uint64_t mbar;
     if (threadIdx.x == 0) {
         mbar_init(&mbar, 1);
@@ -18,7 +20,7 @@ __global__ void k_wait_expires(long long limit, int *expired) {
     __syncthreads();
     // phase 0 never completes: no thread arrives
     const bool done = mbar_wait_bounded(&mbar, 0u, limit);
-    if (threadIdx.x == 0) *expired = done ? 0 : 1;
+    if (threadIdx.x == 0) g_wait_expired = done ? 0 : 1;
 }
 
 }  // namespace mgct
@@ -34,14 +36,12 @@ extern "C" int mgct_check_bounded_wait(double seconds, int *expired, mgct_stream
     MGCT_TRY(check_cuda(cudaGetDevice(&dev), "device"));
     MGCT_TRY(check_cuda(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev), "clock rate"));
     const long long limit = (long long)(seconds * (double)khz * 1e3);
-    int *d = nullptr;
-    MGCT_TRY(check_cuda(cudaMallocAsync(&d, sizeof(int), s), "allocate flag"));
-    int st = check_cuda(cudaMemsetAsync(d, 0, sizeof(int), s), "clear flag");
-    if (!st) {
-        MGCT_KERNEL(KK_OTHER, s, k_wait_expires<<<1, 32, 0, s>>>(limit, d));
-        st = check_cuda(cudaMemcpyAsync(expired, d, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
-    }
-    cudaFreeAsync(d, s);
+    const int zero = 0;
+    MGCT_TRY(check_cuda(cudaMemcpyToSymbolAsync(g_wait_expired, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s),
+                        "clear flag"));
+    MGCT_KERNEL(KK_OTHER, s, k_wait_expires<<<1, 32, 0, s>>>(limit));
+    int st = check_cuda(cudaMemcpyFromSymbolAsync(expired, g_wait_expired, sizeof(int), 0, cudaMemcpyDeviceToHost, s),
+                        "read flag");
     if (!st) st = check_cuda(cudaStreamSynchronize(s), "bounded wait");
     return st;
 }

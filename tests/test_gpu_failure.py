@@ -19,10 +19,11 @@ def built():
 
 def test_bounded_wait_expires_and_reports():
     from paper_2103_10329_gb300 import mgct
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     assert mgct.check_bounded_wait(0.2)
     dt = time.perf_counter() - t0
-    assert 0.1 < dt < 10.0, dt
+    assert 0.15 < dt < 5.0, dt
     # the context is still usable: a convolution pass runs and reports no expiry
     net = mgct.Net(seed=1)
     step = torch.randn((1, 12, 16, 16), device="cuda")

@@ -338,4 +338,197 @@ __global__ void __launch_bounds__(128) k_conv_brick_tc(ConvArgs a, int *err) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05: dw[tap][co][ci] = sum_p gout[p][co] in[p + tap][ci].
+//
+// Per tap it is a GEMM D[co][ci] with K = voxels.  The output tile's gout
+// rows (256 voxels, 2 x 16 x 8) and its haloed input brick are copied into
+// shared memory as 16-byte rows of 8 channels, voxels in (z, y, x) order --
+// which is the MN-major core-matrix layout for this GEMM (8 channels x 8
+// consecutive x voxels per core matrix): the leading byte offset steps the
+// channel chunk, the stride byte offset the next y row (K).  As in the
+// forward, a tap only moves the input operand's start address in the brick.
+// M = 128 rows with Cout of them real: the rows beyond Cout read whatever
+// lies further on in shared memory (the allocation covers them) and land in
+// tensor-memory lanes that are never read.  The accumulators of a group of
+// taps (taps x Cin columns <= 512) stay in tensor memory over the block's
+// voxel tiles (split-K); the block writes its partial sums, which a
+// fixed-order pass adds.  Double-buffered tiles, bounded waits as in the
+// forward.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+struct WgCfg {
+    static constexpr int TPG = (512 / CIN) < 27 ? (512 / CIN) : 27;  // taps per group
+    static constexpr int TG = (27 + TPG - 1) / TPG;                  // tap groups
+    static constexpr int CCI = CIN / 8, CCO = COUT / 8;
+    static constexpr uint32_t A_CS = 256 * 16;                       // gout chunk plane
+    static constexpr uint32_t A_BYTES = CCO * A_CS;
+    static constexpr uint32_t B_BYTES = CCI * BK_CSTR;
+    // the 16 row groups of the second gout buffer's operand must stay inside
+    static constexpr uint32_t REACH = A_BYTES + 17 * A_CS;
+    static constexpr uint32_t USED = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr uint32_t SMEM = (USED > REACH ? USED : REACH) + 1024;
+    static constexpr uint32_t NCOLS = 512;
+};
+
+struct WgArgs {
+    const __nv_bfloat16 *in;    // [nvox][CIN]
+    const __nv_bfloat16 *gout;  // [nvox][COUT]
+    float *part;                // [27][gridDim.x][COUT][CIN]
+    int B, D, H, W;
+};
+
+template <int CIN, int COUT, bool KLBO = true>
+__global__ void __launch_bounds__(128) k_conv_wgrad_tc(WgArgs a, int *err) {
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 128 && CIN <= 256, "tcgen05 shape");
+    using C = WgCfg<CIN, COUT>;
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, CIN) | (1u << 15) | (1u << 16);  // A and B MN-major
+    extern __shared__ unsigned char dsm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+    const uint32_t a_s = smem_u32(base);
+    const uint32_t b_s = a_s + 2 * C::A_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x, g = blockIdx.x;
+    const int tap0 = blockIdx.y * C::TPG;
+    const int ntap = min(C::TPG, 27 - tap0);
+    const BrickTiles T = brick_tiles(a.B, a.D, a.H, a.W);
+    const int my_tiles = g < T.ntiles ? (T.ntiles - 1 - g) / G + 1 : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(C::NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    auto tile_origin = [&](int j, int &b, int &z0, int &y0, int &x0) {
+        int t = g + j * G;
+        x0 = (t % T.ntx) * BK_TX;
+        t /= T.ntx;
+        y0 = (t % T.nty) * BK_TY;
+        t /= T.nty;
+        z0 = (t % T.ntz) * BK_TZ;
+        b = t / T.ntz;
+    };
+    auto load_tile = [&](int j) {
+        int b, z0, y0, x0;
+        tile_origin(j, b, z0, y0, x0);
+        const uint32_t ad = a_s + (j & 1) * C::A_BYTES, bd = b_s + (j & 1) * C::B_BYTES;
+        // gout rows of the tile's own voxels (zero outside the volume)
+        for (int idx = tid; idx < 256 * C::CCO; idx += 128) {
+            const int r = idx / C::CCO, ch = idx % C::CCO;
+            const int z = z0 + r / 128, y = y0 + (r / 8) % 16, x = x0 + r % 8;
+            const bool valid = z < a.D && y < a.H && x < a.W;
+            const size_t q = valid ? (((size_t)b * a.D + z) * a.H + y) * a.W + x : 0;
+            cp_async16(ad + ch * C::A_CS + r * 16, a.gout + q * COUT + ch * 8, valid);
+        }
+        // the input brick with its one-voxel halo (zero outside the volume)
+        for (int idx = tid; idx < BK_ROWS * C::CCI; idx += 128) {
+            const int row = idx / C::CCI, ch = idx % C::CCI;
+            const int xx = row % BK_XB, yy = (row / BK_XB) % BK_YB, zz = row / (BK_XB * BK_YB);
+            const int z = z0 - 1 + zz, y = y0 - 1 + yy, x = x0 - 1 + xx;
+            const bool valid =
+                (unsigned)z < (unsigned)a.D && (unsigned)y < (unsigned)a.H && (unsigned)x < (unsigned)a.W;
+            const size_t q = valid ? (((size_t)b * a.D + z) * a.H + y) * a.W + x : 0;
+            cp_async16(bd + ch * BK_CSTR + row * 16, a.in + q * CIN + ch * 8, valid);
+        }
+    };
+    auto issue_tile = [&](int j) {
+        // MN-major operands: the leading byte offset steps K (the next 8 voxels,
+        // here the next y row), the stride byte offset steps M / N (the next
+        // 8 channels)
+        const uint64_t ad0 = KLBO ? tc_smem_desc(a_s + (j & 1) * C::A_BYTES, 128, C::A_CS)
+                                  : tc_smem_desc(a_s + (j & 1) * C::A_BYTES, C::A_CS, 128);
+        const uint64_t bd0 = KLBO ? tc_smem_desc(b_s + (j & 1) * C::B_BYTES, BK_XB * 16, BK_CSTR)
+                                  : tc_smem_desc(b_s + (j & 1) * C::B_BYTES, BK_CSTR, BK_XB * 16);
+        for (int t = 0; t < ntap; ++t) {
+            const int tap = tap0 + t;
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+            const uint32_t dcol = tmem + t * CIN;
+#pragma unroll
+            for (int zz = 0; zz < BK_TZ; ++zz)
+#pragma unroll
+                for (int yp = 0; yp < BK_TY / 2; ++yp) {
+                    const uint32_t aoff = (zz * 128 + yp * 16) * 16;
+                    const uint32_t boff = (((zz + dz) * BK_YB + 2 * yp + dy) * BK_XB + dx) * 16;
+                    tc_mma(dcol, ad0 + (aoff >> 4), bd0 + (boff >> 4), IDESC,
+                           (j > 0 || zz > 0 || yp > 0) ? 1u : 0u);
+                }
+        }
+        tc_commit(&mbar[j & 1]);
+    };
+
+    bool ok = true;
+    int done = -1, issued = 0;
+    if (my_tiles > 0) {
+        load_tile(0);
+        cp_async_commit();
+    }
+    for (int j = 0; j < my_tiles; ++j) {
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            issue_tile(j);
+        }
+        issued = j + 1;
+        if (j >= 1) {
+            ok = __all_sync(0xffffffffu, ok && mbar_wait_bounded(&mbar[(j - 1) & 1], (uint32_t)(((j - 1) >> 1) & 1)));
+            if (ok) done = j - 1;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (j + 1 < my_tiles) {
+            load_tile(j + 1);
+            cp_async_commit();
+        }
+    }
+    if (ok && my_tiles > 0) {
+        if (__all_sync(0xffffffffu, mbar_wait_bounded(&mbar[(my_tiles - 1) & 1], (uint32_t)(((my_tiles - 1) >> 1) & 1))))
+            done = my_tiles - 1;
+        else
+            ok = false;
+    }
+    cp_async_wait<0>();
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int co = warp * 32 + lane;
+        for (int t = 0; t < ntap; ++t) {
+            float *o = a.part + ((size_t)(tap0 + t) * G + g) * COUT * CIN;
+#pragma unroll
+            for (int c0 = 0; c0 < CIN; c0 += 16) {
+                float v[16];
+                tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * CIN + c0, v);
+                if (co < COUT) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) o[(size_t)co * CIN + c0 + i] = my_tiles > 0 ? v[i] : 0.0f;
+                }
+            }
+        }
+    } else {
+        if (tid == 0) atomicExch(err, 1);
+        const int last = issued - 1;
+        if (tid == 0 && last > done) mbar_wait_bounded(&mbar[last & 1], (uint32_t)((last >> 1) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::NCOLS) : "memory");
+    }
+}
+
 }  // namespace mgct

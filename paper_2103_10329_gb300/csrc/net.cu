@@ -6,10 +6,9 @@
 // channel; its input is the step alpha d scaled to unit RMS, x = alpha d / s,
 // and the corrected step is d' = s (x + f(x)).  Training minimises the mean
 // of (x + f(x) - t)^2 with t = e / s, e the error of the current estimate, by
-// Adam on float32 master weights.  The convolutions run on the BF16 tensor
-// cores with float32 accumulation and BF16 activations: forward and
-// backward-data on tcgen05 (conv3d_tc.cuh), the weight gradient on mma.sync
-// (conv3d.cuh).
+// Adam on float32 master weights.  The convolutions -- forward, backward
+// data and the weight gradient -- run on the tcgen05 tensor cores
+// (conv3d_tc.cuh) with float32 accumulation and BF16 activations.
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -215,24 +214,38 @@ static int conv_bwd_data(int l, const ConvArgs &a, int *err, cudaStream_t s) {
     }
 }
 
-constexpr int WG_BLOCKS = 96;
-constexpr int NET_HALO = 4;  // planes each side a slab needs: four 3x3x3 layers  // voxel-tile groups per tap in the weight gradient
+constexpr int WG_PARTS = 152;  // most blocks per tap of the weight gradient (partial sums kept)
+constexpr int NET_HALO = 4;    // planes each side a slab needs: four 3x3x3 layers
 
+// weight gradient on tcgen05: persistent blocks, (SMs / tap groups) per tap
+// group, capped at WG_PARTS; returns the number of partial sums per tap
 template <int CIN, int COUT>
 static int conv_wgrad_t(const __nv_bfloat16 *in, const __nv_bfloat16 *gout, float *part, int B, int D, int H, int W,
-                        int nvox, cudaStream_t s) {
-    dim3 grid(WG_BLOCKS, 27);
-    MGCT_KERNEL(KK_CONV, s, k_conv_wgrad<CIN, COUT><<<grid, 128, 0, s>>>(in, gout, part, B, D, H, W, nvox));
+                        int *err, int *nparts, cudaStream_t s) {
+    using C = WgCfg<CIN, COUT>;
+    auto kern = k_conv_wgrad_tc<CIN, COUT, true>;
+    static int nsm = 0;  // per instantiation
+    if (!nsm) {
+        MGCT_TRY(check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM),
+                            "wgrad smem"));
+        int dev = 0;
+        MGCT_TRY(check_cuda(cudaGetDevice(&dev), "wgrad device"));
+        MGCT_TRY(check_cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "wgrad SMs"));
+    }
+    const int G = std::max(1, std::min(WG_PARTS, nsm / C::TG));
+    *nparts = G;
+    WgArgs a{in, gout, part, B, D, H, W};
+    MGCT_KERNEL(KK_CONV, s, kern<<<dim3(G, C::TG), 128, C::SMEM, s>>>(a, err));
     return MGCT_OK;
 }
 
 static int conv_wgrad(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *gout, float *part, int B, int D, int H,
-                      int W, int nvox, cudaStream_t s) {
+                      int W, int *err, int *nparts, cudaStream_t s) {
     switch (l) {
-        case 0: return conv_wgrad_t<16, 16>(in, gout, part, B, D, H, W, nvox, s);
-        case 1: return conv_wgrad_t<16, 32>(in, gout, part, B, D, H, W, nvox, s);
-        case 2: return conv_wgrad_t<32, 64>(in, gout, part, B, D, H, W, nvox, s);
-        default: return conv_wgrad_t<64, 16>(in, gout, part, B, D, H, W, nvox, s);
+        case 0: return conv_wgrad_t<16, 16>(in, gout, part, B, D, H, W, err, nparts, s);
+        case 1: return conv_wgrad_t<16, 32>(in, gout, part, B, D, H, W, err, nparts, s);
+        case 2: return conv_wgrad_t<32, 64>(in, gout, part, B, D, H, W, err, nparts, s);
+        default: return conv_wgrad_t<64, 16>(in, gout, part, B, D, H, W, err, nparts, s);
     }
 }
 
@@ -267,7 +280,7 @@ static size_t carve_net(int64_t nvox, bool training, char *base, NetSpace *sp) {
         for (int l = 0; l < NL; ++l) s.g[l] = reinterpret_cast<__nv_bfloat16 *>(take((size_t)nvox * LCOUT[l] * 2));
         size_t mw = 0;
         for (int l = 0; l < NL; ++l) mw = std::max(mw, wcount(l));
-        s.wpart = reinterpret_cast<float *>(take((size_t)WG_BLOCKS * mw * 4));
+        s.wpart = reinterpret_cast<float *>(take((size_t)WG_PARTS * mw * 4));
         s.bpart = reinterpret_cast<float *>(take((size_t)1024 * 64 * 4));
     }
     if (sp) *sp = s;
@@ -541,9 +554,10 @@ int mgct_net_forward_backward(mgct_net *net, int B, int D, int H, int W, const f
     // backward through the layers; g[l] = dL/d(output of layer l)
     for (int l = NL - 1; l >= 0; --l) {
         const __nv_bfloat16 *lin = l == 0 ? sp.x0 : sp.act[l - 1];
-        MGCT_TRY(conv_wgrad(l, lin, sp.g[l], sp.wpart, B, D, H, W, nvox, s));
+        int nparts = 0;
+        MGCT_TRY(conv_wgrad(l, lin, sp.g[l], sp.wpart, B, D, H, W, net->err, &nparts, s));
         const int m = LCOUT[l] * LCIN[l];
-        MGCT_KERNEL(KK_CONV, s, k_sum_wgrad<<<(27 * m + 255) / 256, 256, 0, s>>>(sp.wpart, WG_BLOCKS, m, net->gw[l]));
+        MGCT_KERNEL(KK_CONV, s, k_sum_wgrad<<<(27 * m + 255) / 256, 256, 0, s>>>(sp.wpart, nparts, m, net->gw[l]));
         const int cb = std::min(1024, (nvox + 255) / 256);
         MGCT_KERNEL(KK_CONV, s, k_channel_sums<<<cb, 256, 0, s>>>(sp.g[l], nvox, LCOUT[l], sp.bpart));
         MGCT_KERNEL(KK_CONV, s, k_sum_rows<<<1, 64, 0, s>>>(sp.bpart, cb, LCOUT[l], net->gb[l]));

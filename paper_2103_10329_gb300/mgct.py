@@ -56,6 +56,11 @@ def lib():
     vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     L.mgct_geometry_create.argtypes = [ctypes.POINTER(GeomDesc), ctypes.POINTER(vp)]
     L.mgct_geometry_set_drift.argtypes = [vp, vp]
+    L.mgct_geometry_set_preconditioner.argtypes = [vp, vp]
+    L.mgct_bilateral.argtypes = [i, vp, vp, d, d, i, vp]
+    L.mgct_check_bounded_wait.argtypes = [d, vp, vp]
+    for fn in ("mgct_geometry_set_preconditioner", "mgct_bilateral", "mgct_check_bounded_wait"):
+        getattr(L, fn).restype = ctypes.c_int
     L.mgct_geometry_destroy.argtypes = [vp]
     L.mgct_geometry_destroy.restype = None
     L.mgct_geometry_level.argtypes = [vp, i, vp, vp, vp, vp, vp]
@@ -129,8 +134,6 @@ def check_bounded_wait(seconds: float = 0.2) -> bool:
     """Run the library's bounded device wait on a barrier nothing completes
     (mgct_check_bounded_wait); True when it expired and reported as designed."""
     L = lib()
-    L.mgct_check_bounded_wait.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
-    L.mgct_check_bounded_wait.restype = ctypes.c_int
     flag = ctypes.c_int(0)
     _check(L.mgct_check_bounded_wait(float(seconds), ctypes.byref(flag), _stream()))
     return flag.value == 1
@@ -189,8 +192,6 @@ class Geometry:
         """A [3][3][3] kernel ([dz][dy][dx], applied as a correlation) in place
         of Eq. 5 on every grid; None restores Eq. 5."""
         L = lib()
-        L.mgct_geometry_set_preconditioner.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
-        L.mgct_geometry_set_preconditioner.restype = ctypes.c_int
         if kernel is None:
             _check(L.mgct_geometry_set_preconditioner(self.handle, None))
             return
@@ -413,9 +414,6 @@ def bilateral(x: torch.Tensor, sigma_s: float, sigma_r: float, radius: int, out:
     if out is None:
         out = torch.empty_like(x)
     L = lib()
-    L.mgct_bilateral.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
-                                 ctypes.c_int, ctypes.c_void_p]
-    L.mgct_bilateral.restype = ctypes.c_int
     _check(L.mgct_bilateral(n, _ptr(x, "x", torch.float32), _ptr(out, "out", torch.float32), float(sigma_s),
                             float(sigma_r), int(radius), _stream()))
     return out

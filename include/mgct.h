@@ -143,12 +143,16 @@ int mgct_project(const mgct_geom *geom, int level, int view0, int nviews, int vi
 /* ---------------------------------------------------------------------------
  * Back-projection B = A^T (Sec. 2.1: B is the adjoint of the projection).
  *
- * Voxel-driven gather with the exact transpose of mgct_project's weights:
- * for each voxel and view, every detector pixel whose ray crosses the voxel's
- * plane (along that ray's major axis) within one voxel of it contributes
- * y * h_g|w|/|w_a| * hat(db) * hat(dc).  No atomics: the result is
- * deterministic.  sino: batch sinogram of dtype st; vol_out: float32
- * [n_g]^3, overwritten (accumulate = 0) or added to (accumulate = 1).
+ * The exact transpose of mgct_project's weights: for each voxel and view,
+ * every detector pixel whose ray crosses the voxel's plane (along that ray's
+ * major axis) within one voxel of it contributes
+ * y * h_g|w|/|w_a| * hat(db) * hat(dc).  On tilt-free geometries each ray's
+ * y * h_g|w|/|w_a| is formed in the handle's quad scratch (in chunks of
+ * views) and splatted by z-slab into shared memory; with detector tilt, or a
+ * scratch smaller than one view, a per-voxel gather computes the same sums.
+ * No atomics: the result is deterministic.  sino: batch sinogram of dtype
+ * st; vol_out: float32 [n_g]^3, overwritten (accumulate = 0) or added to
+ * (accumulate = 1).  Uses the handle's scratch.
  * ------------------------------------------------------------------------- */
 int mgct_backproject(const mgct_geom *geom, int level, int view0, int nviews, int view_stride,
                      const void *sino, mgct_dtype st, float *vol_out, int accumulate,

@@ -286,11 +286,17 @@ struct SlabCfg {
     static constexpr int ROWS = Z + 5;  // guard rows: two below, three above (row pairs reach r + 2)
 };
 
-template <int NCH, typename ST>
+// DFA = true: the public A^T at any N.  The column comes from the double-
+// float table and its z crossing is anchored, in double-float, at the detector
+// row nearest the slab's centre, so the crossings are stepped in float32 from
+// a small height relative to the slab (accurate to ~1e-6 voxel at any N; the
+// float32 table's uncentred heights near z = 1000 carry ~6e-5).
+template <int NCH, typename ST, bool DFA = false>
 __global__ void __launch_bounds__(BS_THREADS)
     k_backproject_slab(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
                        float *__restrict__ out, int accumulate) {
     constexpr int Z = SlabCfg<NCH>::Z, ROWS = SlabCfg<NCH>::ROWS;
+    constexpr int CW = DFA ? 4 : 2;  // float4 per table entry
     __shared__ float acc[NCH][ROWS][BS_THREADS];
     const int tid = threadIdx.x;
     const int jx = blockIdx.x * BS_TX + (tid % BS_TX), jy = blockIdx.y * BS_TY + tid / BS_TX;
@@ -316,21 +322,47 @@ __global__ void __launch_bounds__(BS_THREADS)
             const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
             const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
             const ST *__restrict__ sv = sino + (size_t)i * view_elems;
-            const float4 *__restrict__ ct = cols + (size_t)k * a.nu * 2;
+            const float4 *__restrict__ ct = cols + (size_t)k * a.nu * CW;
             for (int ju = ulo; ju <= uhi; ++ju) {
-                const float4 t0 = __ldg(ct + 2 * ju);
-                const float4 t1 = __ldg(ct + 2 * ju + 1);
+                const float4 t0 = __ldg(ct + CW * ju);
+                const float4 t1 = __ldg(ct + CW * ju + 1);
                 const bool ay = t0.x != 0.0f;
                 const float ca = ay ? cy : cx, cb = ay ? cx : cy;
-                const float hb = 1.0f - fabsf(fmaf(ca, t0.y, t0.z) - cb);
-                if (hb <= 0.0f) continue;
-                const float E0 = fmaf(ca, t1.x, t0.w) + ic;  // uncentred z crossing at v' = 0
-                const float E1 = fmaf(ca, t1.z, t1.y);
-                const float rE = __frcp_rn(E1);
-                const float ta = fmaf(zlo - E0, rE, cv), tb = fmaf(zhi - E0, rE, cv);
-                const int vlo = max(0, (int)ceilf(fminf(ta, tb) - 1e-3f));
-                const int vhi = min(a.nv - 1, (int)floorf(fmaxf(ta, tb) + 1e-3f));
-                float vf = (float)vlo - cv;
+                // E0, E1: crossing height at row offset vf = 0 and its slope per
+                // row; zb: the height E0 is counted from (uncentred z)
+                float hb, E0, E1, vf;
+                int vlo, vhi, zb;
+                if constexpr (!DFA) {
+                    hb = 1.0f - fabsf(fmaf(ca, t0.y, t0.z) - cb);
+                    if (hb <= 0.0f) continue;
+                    E0 = fmaf(ca, t1.x, t0.w) + ic;  // uncentred z crossing at v' = 0
+                    E1 = fmaf(ca, t1.z, t1.y);
+                    const float rE = __frcp_rn(E1);
+                    const float ta = fmaf(zlo - E0, rE, cv), tb = fmaf(zhi - E0, rE, cv);
+                    vlo = max(0, (int)ceilf(fminf(ta, tb) - 1e-3f));
+                    vhi = min(a.nv - 1, (int)floorf(fmaxf(ta, tb) + 1e-3f));
+                    vf = (float)vlo - cv;
+                    zb = z0;
+                } else {
+                    const float4 t2 = __ldg(ct + CW * ju + 2), t3 = __ldg(ct + CW * ju + 3);
+                    const DF eb = df_add(df_mul_f(DF{t0.y, t0.z}, ca), DF{t0.w, t1.x});
+                    hb = 1.0f - fabsf(__fadd_rn(__fsub_rn(eb.hi, cb), eb.lo));
+                    if (hb <= 0.0f) continue;
+                    const DF Eb = df_add(DF{t1.y, t1.z}, df_mul_f(DF{t1.w, t2.x}, ca));   // centred, v' = 0
+                    const DF E1d = df_add(DF{t2.y, t2.z}, df_mul_f(DF{t2.w, t3.x}, ca));
+                    E1 = E1d.hi;
+                    const float zc = (float)z0 - ic + 0.5f * (float)(Z - 1);  // slab centre, centred (exact)
+                    const float va = rintf((zc - Eb.hi) / E1);                // anchor row, centred v'
+                    if (!(fabsf(va) < 1.0e7f)) continue;
+                    const DF c = df_add(df_add(Eb, df_mul_f(E1d, va)), DF{-zc, 0.0f});
+                    E0 = (c.hi + c.lo) + 0.5f * (float)(Z - 1);  // height above z0 at the anchor row
+                    const float rE = __frcp_rn(E1);
+                    const float ta = fmaf(-1.0f - E0, rE, va + cv), tb = fmaf((float)Z - E0, rE, va + cv);
+                    vlo = max(0, (int)ceilf(fminf(ta, tb) - 1e-3f));
+                    vhi = min(a.nv - 1, (int)floorf(fmaxf(ta, tb) + 1e-3f));
+                    vf = ((float)vlo - cv) - va;  // rows from the anchor (exact)
+                    zb = 0;
+                }
                 const ST *__restrict__ px = sv + (size_t)vlo * a.nu + ju;
                 int jv = vlo;
                 if constexpr (NCH == 1) {
@@ -342,7 +374,7 @@ __global__ void __launch_bounds__(BS_THREADS)
                         const float fz0 = fmaf(vf, E1, E0), fz1 = fmaf(vf + 1.0f, E1, E0);
                         const float fl0 = floorf(fz0), fl1 = floorf(fz1);
                         const float t0 = fz0 - fl0, t1 = fz1 - fl1;
-                        const int r = min(max((int)fl0 - z0 + 2, 0), ROWS - 3);
+                        const int r = min(max((int)fl0 - zb + 2, 0), ROWS - 3);
                         const bool same = fl1 == fl0;
                         const float y0 = hb * to_f32(__ldg(px)), y1 = hb * to_f32(__ldg(px + a.nu));
                         const float a0 = y0 * t0, b0 = y1 * t1;
@@ -358,7 +390,7 @@ __global__ void __launch_bounds__(BS_THREADS)
                     const float fl = floorf(fz);
                     const float t = fz - fl;
                     // row of voxel floor(fz) in the guarded slab: in [0, Z + 2]
-                    const int r = min(max((int)fl - z0 + 2, 0), ROWS - 2);
+                    const int r = min(max((int)fl - zb + 2, 0), ROWS - 2);
                     if constexpr (NCH == 1) {
                         const float yw = hb * to_f32(__ldg(px));
                         const float w1 = yw * t;
@@ -466,6 +498,67 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
         MGCT_KERNEL(KK_BACKPROJECT, s,
                     k_backproject<NCH, ST, WEIGHTED><<<grid, dim3(BP_BX, BP_BY, BP_BZ), 0, s>>>(a, sino, out, accumulate));
     }
+    return MGCT_OK;
+}
+
+// The public A^T on tilt-free geometries.  Each ray's path length per plane,
+// dl = h sqrt(1 + rb^2 + rz^2) (the projector's weight; rb per column, rz
+// linear in v', both from the double-float column table), is applied to the
+// caller's sinogram in one pass over it, written to the handle's quad scratch,
+// and the weighted rows are splatted by the double-float-anchored slab
+// kernel: the solver's scatter, for one extra read and write of the sinogram.
+template <typename ST>
+__global__ void k_weight_rays(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
+                              float *__restrict__ w) {
+    const int ju = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ju >= a.nu) return;
+    const int jv = blockIdx.y, i = blockIdx.z;
+    const int k = a.view0 + i * a.stride;
+    const float *c = reinterpret_cast<const float *>(cols + ((size_t)k * a.nu + ju) * 4);
+    const float rb = __ldg(c + 1), ezc = __ldg(c + 7), e1c = __ldg(c + 11);  // rb, (Wc_z + u' Eu_z)/w_a, Ev_z/w_a
+    const float rz = fmaf((float)jv - 0.5f * (float)(a.nv - 1), e1c, ezc);
+    const float dl = sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
+    const size_t idx = ((size_t)i * a.nv + jv) * a.nu + ju;
+    w[idx] = dl * to_f32(__ldg(sino + idx));
+}
+
+// Runs the public A^T through k_weight_rays and the slab kernel, in chunks of
+// views that fit the quad scratch, and sets *ran; leaves *ran = 0 (nothing
+// launched) where it does not apply: tilted detectors, no views, or a
+// scratch smaller than one view.
+template <typename ST>
+int launch_backproject_public(const mgct_geom *g, int level, int view0, int nviews, int stride, const ST *sino,
+                              float *out, int accumulate, cudaStream_t s, int *ran) {
+    *ran = 0;
+    const LevelInfo &L = g->lev[level];
+    const size_t view_elems = (size_t)L.nu * L.nv;
+    const size_t cap = 2 * quad_elems(g->lev[0].n) * 4;  // floats in the quad scratch
+    if (!g->separable || !L.d_cols_df || nviews < 1 || cap < view_elems || L.nv > 65535) return MGCT_OK;
+    size_t chunk = cap / view_elems;
+    if (chunk > (size_t)nviews) chunk = nviews;
+    if (chunk > 65535) chunk = 65535;
+    float *w = static_cast<float *>(g->d_scratch_quads);
+    BPArgs a;
+    a.views = L.d_views;
+    a.n = L.n;
+    a.nu = L.nu;
+    a.nv = L.nv;
+    a.h = (float)L.h;
+    a.stride = stride;
+    constexpr int Z = SlabCfg<1>::Z;
+    const dim3 grid((L.n + BS_TX - 1) / BS_TX, (L.n + BS_TY - 1) / BS_TY, (L.n + Z - 1) / Z);
+    for (int c0 = 0; c0 < nviews; c0 += (int)chunk) {
+        const int cn = nviews - c0 < (int)chunk ? nviews - c0 : (int)chunk;
+        a.view0 = view0 + c0 * stride;
+        a.nviews = cn;
+        const dim3 wgrid((L.nu + 127) / 128, L.nv, cn);
+        MGCT_KERNEL(KK_BACKPROJECT, s,
+                    k_weight_rays<ST><<<wgrid, 128, 0, s>>>(a, L.d_cols_df, sino + (size_t)c0 * view_elems, w));
+        MGCT_KERNEL(KK_BACKPROJECT, s,
+                    k_backproject_slab<1, float, true><<<grid, BS_THREADS, 0, s>>>(a, L.d_cols_df, w, out,
+                                                                                    (accumulate || c0) ? 1 : 0));
+    }
+    *ran = 1;
     return MGCT_OK;
 }
 

@@ -445,6 +445,25 @@ int mgct_backproject(const mgct_geom *g, int level, int view0, int nviews, int s
     MGCT_TRY(check_ptr(sino, "sino", nviews == 0));
     MGCT_TRY(check_ptr(vol_out, "vol_out"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int ran = 0;
+    switch (st) {
+        case MGCT_F32:
+            MGCT_TRY(launch_backproject_public<float>(g, level, view0, nviews, stride,
+                                                      static_cast<const float *>(sino), vol_out, accumulate, s, &ran));
+            break;
+        case MGCT_BF16:
+            MGCT_TRY(launch_backproject_public<__nv_bfloat16>(g, level, view0, nviews, stride,
+                                                              static_cast<const __nv_bfloat16 *>(sino), vol_out,
+                                                              accumulate, s, &ran));
+            break;
+        case MGCT_F16:
+            MGCT_TRY(launch_backproject_public<__half>(g, level, view0, nviews, stride,
+                                                       static_cast<const __half *>(sino), vol_out, accumulate, s,
+                                                       &ran));
+            break;
+        default: break;
+    }
+    if (ran) return MGCT_OK;
     switch (st) {
         case MGCT_F32:
             return launch_backproject<1, float>(g, level, view0, nviews, stride, static_cast<const float *>(sino),

@@ -163,6 +163,29 @@ def test_backproject_subset_and_storage_dtypes():
     assert e16.max() <= TOL_F32, summary(e16)
 
 
+@pytest.mark.parametrize("case", ["chunked", "scratch_too_small"])
+def test_backproject_chunks_and_fallback(case):
+    """The public A^T weights the caller's rays into the quad scratch,
+    8 (n+5)^2 n floats, and splats them with the slab kernel.  At n = 16 with
+    a 48^2 detector the scratch holds 24 views, so 60 views run as chunks of
+    24, 24 and 12 (the later ones accumulating); at n = 8 with a 112^2
+    detector it holds less than one view and the call takes the per-voxel
+    gather instead.  Both against the oracle, plain and accumulating."""
+    n, nu, k = (16, 48, 60) if case == "chunked" else (8, 112, 6)
+    d = scan_desc(n, nu, nu, k, 41, levels=1)
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    y = np.random.default_rng(42).random((k, nu, nu)).astype(np.float32)
+    ref = O.backproject(og, y.astype(np.float64))
+    got = to_np(mgct.backproject(g, cuda(y)))
+    e = rel_err(got, ref)
+    assert e.max() <= TOL_F32, summary(e)
+    out = torch.full((n, n, n), 0.5, device="cuda")
+    got = to_np(mgct.backproject(g, cuda(y), out=out, accumulate=True)) - 0.5
+    e = rel_err(got, ref)
+    assert e.max() <= 2 * TOL_F32, summary(e)
+
+
 def test_backproject_empty_selection_gives_zero():
     d = c1_desc(n=32, nu=48, nv=48, nviews=10)
     g = gpu_geom(d)

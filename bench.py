@@ -253,13 +253,17 @@ def roi_rmse(vol, truth):
 # ---------------------------------------------------------------------------
 # the oracle on host cores (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(name, target_s=15.0, vol=None, views_cap=None):
+def oracle_sample(name, target_s=15.0, vol=None, views_cap=None, dims=None):
     """A and A^T of the FP64 oracle at grid 0 on a sample of views; returns
-    (GUPS, seconds, views used, threads)."""
+    (GUPS, seconds, views used, threads, seconds of A, seconds of A^T).
+    `dims` = (n, detector, views) overrides the workload's sizes."""
     import oracle as O
     from paper_2103_10329_gb300 import synth
-    w = WORKLOADS[name]
-    n, nu, K = w["n"], w["nu"], w["views"]
+    if dims is None:
+        w = WORKLOADS[name]
+        n, nu, K = w["n"], w["nu"], w["views"]
+    else:
+        n, nu, K = dims
     th, z = synth.trajectory(K, SEED + 1)
     scan = O.Scan(n=n, nu=nu, nv=nu, theta=th, z=z, pitch=synth.default_pitch(nu))
     g = O.level_geometry(scan, 0)
@@ -273,17 +277,17 @@ def oracle_sample(name, target_s=15.0, vol=None, views_cap=None):
         t1 = time.perf_counter()
         O.backproject(gs, y)
         t2 = time.perf_counter()
-        return t2 - t0
+        return t2 - t0, t1 - t0, t2 - t1
 
     cnt = min(4, K)
-    t = run(cnt)
+    t = run(cnt)[0]
     if views_cap is None:
         cnt2 = int(max(cnt, min(K, cnt * target_s / max(t, 1e-3))))
     else:
         cnt2 = min(views_cap, K)
-    t = run(cnt2)
+    t, ta, tat = run(cnt2)
     gups = 2.0 * n ** 3 * cnt2 / t / 1e9
-    return gups, t, cnt2, O.num_threads()
+    return gups, t, cnt2, O.num_threads(), ta, tat
 
 
 def reference_arm(args, rank):
@@ -299,7 +303,7 @@ def reference_arm(args, rank):
     per_step_views = args.ref_views
     vals = []
     for i in range(args.warmup + args.steps):
-        gups, t, cnt, thr = oracle_sample(name, vol=vol, views_cap=per_step_views)
+        gups, t, cnt, thr, _, _ = oracle_sample(name, vol=vol, views_cap=per_step_views)
         if i >= args.warmup:
             vals.append((gups, t))
     tot_t = sum(t for _, t in vals)
@@ -315,6 +319,218 @@ def reference_arm(args, rank):
                                        f"views per step"},
             "e2e": {"value": value, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _event_ms(fn, reps, warm=1):
+    """Median CUDA-event time (ms) of fn() on the current stream."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _oracle_solve_units(n, views, levels, iters=2):
+    """Voxel-view counts of the oracle's A and A^T calls in `iters` multigrid
+    iterations: Landweber on grids 0..L-2 takes two A (residual, line search)
+    and one A^T; its OS-EMTR pass on the coarsest grid takes two A (P 1 and the
+    subsets' forward projections) and two A^T (numerator, denominator)."""
+    ua = uat = 0
+    for g in range(levels):
+        u = (n >> g) ** 3 * views
+        if levels == 1 or g < levels - 1:
+            ua, uat = ua + 2 * u, uat + u
+        else:
+            ua, uat = ua + 2 * u, uat + 2 * u
+    return iters * ua, iters * uat
+
+
+def _ray_voxel_rates(og, vol, samples, sino_views=8):
+    """Oracle seconds per ray of A and per voxel-view of A^T, from `samples`
+    random rays (project_rays on `vol`) and random voxels over `sino_views`
+    views (backproject_voxels on a random sinogram)."""
+    import oracle as O
+    from paper_2103_10329_gb300 import synth
+    K = og.n_views
+    rays = synth.random_indices(samples, (K, og.nv, og.nu), SEED + 11)
+    t0 = time.perf_counter()
+    O.project_rays(og, vol, rays)
+    t_ray = (time.perf_counter() - t0) / samples
+    sub = og.subset(np.arange(0, K, max(1, K // sino_views))[:sino_views])
+    y = synth.random_sino(sub.n_views, og.nv, og.nu, SEED + 12)
+    vox = synth.random_indices(samples, (og.n,) * 3, SEED + 13)
+    t0 = time.perf_counter()
+    O.backproject_voxels(sub, y, vox, radius=5)
+    t_vox = (time.perf_counter() - t0) / (samples * sub.n_views)
+    return t_ray, t_vox
+
+
+def oracle_beside(c2_sample, c2_gpu, full_c2=False, samples=100000):
+    """The FP64 oracle timed beside the GPU, on the host cores, per operation
+    (one A and one A^T over every view, at grid 0) and per solve (two multigrid
+    iterations from zero):
+      64^3 / 96^2 / 90 views / 2 grids   both sides measured in full;
+      256^3 / 384^2 / 720 views / 3 grids  oracle A and A^T on a sample of
+          views scaled to all views (exact: views are independent), its solve
+          extrapolated from those rates (measured in full with full_c2);
+      512^3 / 768^2 / 1440 views          oracle on a sample of views;
+      1024^3 / 1536^2 / 2880 views        oracle extrapolated by its per-nonzero
+          rate at 512^3.
+    Beside each view sample, the time extrapolated from random rays
+    (project_rays) and random voxels (backproject_voxels) is reported as a
+    check: the per-voxel routine evaluates the per-entry weight over a pixel
+    window, far slower than the oracle's scatter A^T, so those rates do not
+    stand for the whole calls.  GPU times are CUDA-event medians of the
+    library's public calls."""
+    import torch
+    import oracle as O
+    from paper_2103_10329_gb300 import mgct, synth
+    out = {"threads": O.num_threads(), "host_cores": len(os.sched_getaffinity(0)),
+           "timing": "oracle: wall clock, FP64, all host threads; GPU: CUDA events, FP32, median", "configs": {}}
+
+    def scan_of(n, nu, K):
+        th, z = synth.trajectory(K, SEED + 1)
+        return O.Scan(n=n, nu=nu, nv=nu, theta=th, z=z, pitch=synth.default_pitch(nu)), th, z
+
+    def per_op(o_a, o_at, g_a, g_at, how):
+        return {"A": {"oracle_s": o_a, "gpu_ms": g_a, "speedup": o_a * 1e3 / g_a},
+                "AT": {"oracle_s": o_at, "gpu_ms": g_at, "speedup": o_at * 1e3 / g_at}, "oracle": how}
+
+    def gpu_ops(g, vol, reps, warm=1):
+        y = mgct.project(g, vol)
+        t_a = _event_ms(lambda: mgct.project(g, vol, out=y), reps, warm)
+        vo = torch.empty_like(vol)
+        t_at = _event_ms(lambda: mgct.backproject(g, y, out=vo), reps, warm)
+        return t_a, t_at
+
+    def gpu_solve(g, b, reps=3):
+        rec = mgct.Reconstructor(g)
+        rec.prepare(b)
+        n = g.n
+        v = torch.zeros((n, n, n), device="cuda")
+
+        def run():
+            v.zero_()
+            rec.iterate(v)
+            rec.iterate(v)
+        t = _event_ms(run, reps)
+        return t, v
+
+    # --- 64^3: everything measured on both sides
+    w = WORKLOADS["c1"]
+    n, nu, K, L = w["n"], w["nu"], w["views"], w["levels"]
+    W = make_workload("c1")
+    g, b, truth = W["geom"], W["b"], W["truth"]
+    vol = synth.random_volume(n, SEED)
+    ga, gat = gpu_ops(g, torch.as_tensor(vol, dtype=torch.float32, device="cuda"), 10, 3)
+    scan, th, z = scan_of(n, nu, K)
+    og = O.level_geometry(scan, 0)
+    ta = min(_timed(lambda: O.project(og, vol)) for _ in range(3))
+    y = O.project(og, vol)
+    tat = min(_timed(lambda: O.backproject(og, y)) for _ in range(3))
+    gs_ms, vg = gpu_solve(g, b)
+    ph = synth.ellipsoids(w["count"], SEED, axis_lo=w["axis"][0], axis_hi=w["axis"][1])
+    fine = synth.voxelize_ellipsoids(ph, 2 * n, supersample=1, device="cpu", dtype=torch.float64).numpy()
+    b_or = O.project(O.level_geometry(scan_of(2 * n, nu, K)[0], 0), fine)
+    t0 = time.perf_counter()
+    vo = O.reconstruct(scan, b_or, iters=2, levels=L)
+    ts = time.perf_counter() - t0
+    ua, uat = _oracle_solve_units(n, K, L)
+    ext = ua * ta / (n ** 3 * K) + uat * tat / (n ** 3 * K)
+    out["configs"]["64^3/96^2/90 views/2 grids"] = {
+        "per_op": per_op(ta, tat, ga, gat, "measured, whole call (best of 3)"),
+        "per_solve": {"oracle_s": ts, "gpu_ms": gs_ms, "speedup": ts * 1e3 / gs_ms, "oracle": "measured",
+                      "oracle_extrapolated_s": ext,
+                      "rmse_roi": {"oracle": roi_rmse(torch.from_numpy(vo).float(), truth.cpu()),
+                                   "gpu": roi_rmse(vg, truth)},
+                      "data": "each side projects the same 128^3 phantom with its own A"}}
+    g.close()
+    del W, b, truth, vg
+
+    # --- the bench workload: oracle per-op from the view sample of the CPU baseline
+    w = WORKLOADS["c2"]
+    n, nu, K, L = w["n"], w["nu"], w["views"], w["levels"]
+    cnt, s_a, s_at, vol2 = c2_sample
+    ta, tat = s_a * K / cnt, s_at * K / cnt
+    g, b = c2_gpu
+    ga, gat = gpu_ops(g, torch.as_tensor(vol2, dtype=torch.float32, device="cuda"), 3)
+    gs_ms, _ = gpu_solve(g, b)
+    scan, th, z = scan_of(n, nu, K)
+    og = O.level_geometry(scan, 0)
+    r_ray, r_vox = _ray_voxel_rates(og, vol2, samples)
+    ua, uat = _oracle_solve_units(n, K, L)
+    solve = {"gpu_ms": gs_ms, "oracle_extrapolated_s": ua * ta / (n ** 3 * K) + uat * tat / (n ** 3 * K)}
+    if full_c2:
+        b_or = O.project(og, vol2)
+        t0 = time.perf_counter()
+        O.reconstruct(scan, b_or, iters=2, levels=L)
+        solve["oracle_s"] = time.perf_counter() - t0
+        solve["oracle"] = "measured on b = A x (the oracle's A; solve time does not depend on the data)"
+    else:
+        solve["oracle"] = "extrapolated from the per-operation rates (A and A^T calls only)"
+    solve["speedup"] = solve.get("oracle_s", solve["oracle_extrapolated_s"]) * 1e3 / gs_ms
+    rays_ext = {"A_s": r_ray * K * nu * nu, "AT_s": r_vox * n ** 3 * K}
+    out["configs"]["256^3/384^2/720 views/3 grids"] = {
+        "per_op": per_op(ta, tat, ga, gat, f"measured on {cnt} of {K} views, scaled to all views"),
+        "per_solve": solve, "ray_voxel_extrapolation_check": rays_ext}
+
+    # --- 512^3: oracle on a sample of views, GPU whole calls
+    n, nu, K = 512, 768, 1440
+    vol = synth.random_volume(n, SEED)
+    gups, t, cnt, _, s_a, s_at = oracle_sample(None, target_s=8.0, vol=vol, dims=(n, nu, K))
+    ta, tat = s_a * K / cnt, s_at * K / cnt
+    scan, th, z = scan_of(n, nu, K)
+    og = O.level_geometry(scan, 0)
+    r_ray, r_vox = _ray_voxel_rates(og, vol, samples)
+    g = mgct.Geometry(n, nu, nu, th, z, synth.default_pitch(nu), levels=1)
+    ga, gat = gpu_ops(g, torch.as_tensor(vol, dtype=torch.float32, device="cuda"), 3)
+    g.close()
+    del vol
+    torch.cuda.empty_cache()
+    out["configs"]["512^3/768^2/1440 views"] = {
+        "per_op": per_op(ta, tat, ga, gat, f"measured on {cnt} of {K} views, scaled to all views"),
+        "ray_voxel_extrapolation_check": {"A_s": r_ray * K * nu * nu, "AT_s": r_vox * n ** 3 * K}}
+    nnz3, ta3, tat3 = K * nu * nu * n, ta, tat
+
+    # --- 1024^3: oracle extrapolated from random rays and voxels
+    n, nu, K = 1024, 1536, 2880
+    scan, th, z = scan_of(n, nu, K)
+    og = O.level_geometry(scan, 0)
+    vol = np.full((n, n, n), 0.5)
+    r_ray, r_vox = _ray_voxel_rates(og, vol, samples)
+    del vol
+    g = mgct.Geometry(n, nu, nu, th, z, synth.default_pitch(nu), levels=1)
+    gv = torch.full((n, n, n), 0.5, device="cuda")
+    y = torch.empty((K, nu, nu), device="cuda")
+    mgct.project(g, gv, views=(0, 1, 1), out=y[:1])
+    ga = _event_ms(lambda: mgct.project(g, gv, out=y), 1, 0)
+    mgct.backproject(g, y[:1].contiguous(), views=(0, 1, 1))
+    gat = _event_ms(lambda: mgct.backproject(g, y, out=gv), 1, 0)
+    g.close()
+    del gv, y
+    torch.cuda.empty_cache()
+    f = K * nu * nu * n / nnz3
+    out["configs"]["1024^3/1536^2/2880 views"] = {
+        "per_op": per_op(ta3 * f, tat3 * f, ga, gat,
+                         f"extrapolated by the per-nonzero rate measured at 512^3 (nonzeros of A grow as "
+                         f"views x pixels x n: {f:.0f}x)"),
+        "ray_voxel_extrapolation_check": {"A_s": r_ray * K * nu * nu, "AT_s": r_vox * n ** 3 * K},
+        "volume": "constant 0.5 on both sides"}
+    return out
+
+
+def _timed(fn):
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
 
 
 # ---------------------------------------------------------------------------
@@ -706,14 +922,16 @@ def gpu_arm(args, rank, world):
         hbm = hbm_kernel_rates(peaks.get("hbm_gbs", 6790.0))
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
-    cpu = None
+    cpu = beside = None
     if not args.no_cpu and rank == 0 and world == 1:
         import oracle as O
         O.build()
-        gups, t, cnt, thr = oracle_sample(args.workload, target_s=args.cpu_seconds,
-                                          vol=truth.double().cpu().numpy())
+        vol_np = truth.double().cpu().numpy()
+        gups, t, cnt, thr, ta, tat = oracle_sample(args.workload, target_s=args.cpu_seconds, vol=vol_np)
         cpu = {"value": gups, "unit": "GUPS", "cores": thr, "kind": "oracle",
                "sample": f"FP64 oracle A and A^T at grid 0 on {cnt} of {K} views ({t:.1f} s)"}
+        if not args.no_beside and args.workload == "c2":
+            beside = oracle_beside((cnt, ta, tat, vol_np), (g, b), full_c2=args.oracle_full)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": world, "steps": args.steps,
@@ -721,7 +939,8 @@ def gpu_arm(args, rank, world):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(workload_config(args.workload), parallelism=f"replicas x{world}"),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "kernels": kernels, "hbm_kernels": hbm, "time_to_accuracy": tta}
+                "clocks": clk, "kernels": kernels, "hbm_kernels": hbm, "time_to_accuracy": tta,
+                "oracle_beside": beside}
         print(json.dumps(line), flush=True)
     g.close()
 
@@ -738,6 +957,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-views", type=int, default=8)
+    ap.add_argument("--no-beside", action="store_true",
+                    help="skip the oracle-beside-GPU timings at 64^3, 256^3, 512^3 and 1024^3")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="time the oracle's whole two-iteration solve at 256^3 (minutes of CPU)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-hbm", action="store_true", help="skip the HBM-bound kernel rates at 512^3")
     ap.add_argument("--no-literal", action="store_true",

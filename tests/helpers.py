@@ -1,5 +1,8 @@
 """Shared test helpers: seeded scan descriptions handed to both the oracle
 and the CUDA binding, and the error metrics the parity tests report."""
+import json
+import os
+
 import numpy as np
 import torch
 
@@ -39,6 +42,25 @@ def rel_err(got, ref, floor_frac=1e-2):
 
 def summary(e):
     return f"p50={np.percentile(e, 50):.2e} p99={np.percentile(e, 99):.2e} max={e.max():.2e}"
+
+
+def check_err(e, tol, bound="max"):
+    """Asserts max(e) <= tol (bound "max") or sqrt(mean(e^2)) <= tol (bound
+    "rms").  With MGCT_PARITY_REPORT set to a file path, first appends the
+    test's p50, p99, max and rms of e and the bound to it as one JSON line."""
+    e = np.asarray(e, dtype=np.float64)
+    rms = float(np.sqrt(np.mean(e ** 2))) if e.size else 0.0
+    path = os.environ.get("MGCT_PARITY_REPORT")
+    if path and e.size:
+        rec = {"test": os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], "n": int(e.size),
+               "p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)), "max": float(e.max()),
+               "rms": rms, "bound": bound, "tol": float(tol)}
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+    if bound == "max":
+        assert e.max() <= tol, summary(e)
+    else:
+        assert rms <= tol, f"rms={rms:.2e} " + summary(e)
 
 
 def to_np(t: torch.Tensor):

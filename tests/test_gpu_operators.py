@@ -6,7 +6,7 @@ import torch
 
 import oracle as O
 from paper_2103_10329_gb300 import synth
-from tests.helpers import TOL_F32, cuda, gpu_geom, oracle_scan, rel_err, scan_desc, summary, to_np
+from tests.helpers import TOL_F32, check_err, cuda, gpu_geom, oracle_scan, rel_err, scan_desc, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,7 @@ def test_project_c1(which):
     ref = O.project(og, vol32.astype(np.float64))
     got = to_np(mgct.project(g, cuda(vol32)))
     e = rel_err(got, ref)
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)
 
 
 def test_project_ragged_drift_tilt():
@@ -64,7 +64,7 @@ def test_project_ragged_drift_tilt():
     ref = O.project(og, vol.astype(np.float64))
     got = to_np(mgct.project(g, cuda(vol)))
     e = rel_err(got, ref)
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)
 
 
 def test_project_coarse_level_and_view_subset():
@@ -76,7 +76,7 @@ def test_project_coarse_level_and_view_subset():
     ref = O.project(og1.subset(views), vol.astype(np.float64))
     got = to_np(mgct.project(g, cuda(vol), level=1, views=(3, len(views), 8)))
     e = rel_err(got, ref)
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)
 
 
 def test_project_residual_and_norm():
@@ -105,7 +105,7 @@ def test_project_storage_dtypes(vt, ot):
     got = to_np(mgct.project(g, vol, out_dtype=ot))
     e = rel_err(got, ref)
     tol = {torch.float32: TOL_F32, torch.bfloat16: 2 ** -8, torch.float16: 2 ** -11}[ot]
-    assert e.max() <= tol, summary(e)
+    check_err(e, tol)
 
 
 def test_project_empty_selection():
@@ -132,7 +132,7 @@ def test_backproject_c1(kind):
     # magnitudes of its terms, A^T |y| (equal to |A^T y| for y >= 0)
     scale = O.backproject(og, np.abs(y32.astype(np.float64)))
     e = rel_err(got, ref) if kind == "uniform" else np.abs(got - ref) / np.maximum(scale, 1e-2 * scale.max())
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)
 
 
 def test_backproject_ragged_drift_tilt_and_accumulate():
@@ -144,7 +144,7 @@ def test_backproject_ragged_drift_tilt_and_accumulate():
     out = torch.full((24, 24, 24), 0.5, device="cuda")
     got = to_np(mgct.backproject(g, cuda(y), out=out, accumulate=True)) - 0.5
     e = rel_err(got, ref)
-    assert e.max() <= 2 * TOL_F32, summary(e)
+    check_err(e, 2 * TOL_F32)
 
 
 def test_backproject_subset_and_storage_dtypes():
@@ -156,11 +156,11 @@ def test_backproject_subset_and_storage_dtypes():
     ref = O.backproject(og.subset(views), to_np(y))
     got = to_np(mgct.backproject(g, y, views=(2, len(views), 5)))
     e = rel_err(got, ref)
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)
     y16 = y.to(torch.float16)
     got16 = to_np(mgct.backproject(g, y16, views=(2, len(views), 5)))
     e16 = rel_err(got16, O.backproject(og.subset(views), to_np(y16)))
-    assert e16.max() <= TOL_F32, summary(e16)
+    check_err(e16, TOL_F32)
 
 
 @pytest.mark.parametrize("case", ["chunked", "scratch_too_small"])
@@ -179,11 +179,11 @@ def test_backproject_chunks_and_fallback(case):
     ref = O.backproject(og, y.astype(np.float64))
     got = to_np(mgct.backproject(g, cuda(y)))
     e = rel_err(got, ref)
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)
     out = torch.full((n, n, n), 0.5, device="cuda")
     got = to_np(mgct.backproject(g, cuda(y), out=out, accumulate=True)) - 0.5
     e = rel_err(got, ref)
-    assert e.max() <= 2 * TOL_F32, summary(e)
+    check_err(e, 2 * TOL_F32)
 
 
 def test_backproject_empty_selection_gives_zero():
@@ -242,7 +242,7 @@ def test_full_size_sampled(cfg):
     got = to_np(proj[ri[:, 0], ri[:, 1], ri[:, 2]])
     full_max = float(proj.abs().max())
     e = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * full_max)
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)
     del vol, proj, vol_np
     stride = 40 if n >= 1024 else 1
     views = (0, len(range(0, nviews, stride)), stride)
@@ -255,7 +255,7 @@ def test_full_size_sampled(cfg):
     vi = torch.as_tensor(vox, device="cuda", dtype=torch.long)
     gotv = to_np(bp[vi[:, 2], vi[:, 1], vi[:, 0]])
     ev = np.abs(gotv - refv) / np.maximum(np.abs(refv), 1e-2 * float(bp.abs().max()))
-    assert ev.max() <= TOL_F32, summary(ev)
+    check_err(ev, TOL_F32)
 
 
 # --------------------------------------------------------------------------- p, R, P
@@ -309,4 +309,4 @@ def test_solver_backprojection_full_size_sampled(cfg):
     got = to_np(step[vi[:, 2], vi[:, 1], vi[:, 0]]) / alpha
     ref = O.backproject_voxels(og, to_np(y), vox, radius=5)
     e = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * float(step.abs().max()) / alpha)
-    assert e.max() <= TOL_F32, summary(e)
+    check_err(e, TOL_F32)

@@ -32,6 +32,7 @@ struct BPArgs {
     int n, nu, nv;
     float h;
     int view0, stride, nviews;
+    int splits;  // slab kernel: view ranges per z-slab, each into its own partial volume (1: none)
 };
 
 template <int NCH, typename ST>
@@ -58,7 +59,12 @@ __device__ __forceinline__ float2 load_f2(const ST *) { return make_float2(0.0f,
 // Adds A^T (one view) at voxel (jx, jy, jz) into acc -- any geometry.
 // WEIGHTED: the sinogram already carries each ray's dl (see the projector's
 // weighted epilogues), so the weight is hat * hat; otherwise dl is computed
-// per pixel.  Sinograms are [view][v][u].
+// per pixel.  Sinograms are [view][v][u].  Each candidate ray is set up as
+// the projector sets it up: direction, slopes and centred crossing in
+// double-float from the view table's double-float fields (G must hold them),
+// and the crossing's offset from the voxel, p + c_a r - c, formed in
+// double-float before it is rounded -- in float32 alone the numerators'
+// cancellation leaves ~1e-6 voxel, 1e-5 of a weight near a hat's edge.
 template <int NCH, typename ST, bool WEIGHTED>
 __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int jx, int jy, int jz,
                                         const ST *__restrict__ sino_view, float (&acc)[NCH]) {
@@ -85,22 +91,26 @@ __device__ __forceinline__ void bp_view(const ViewGeom &G, const BPArgs &a, int 
         for (int ju = ulo; ju <= uhi; ++ju) {
             const float up = (float)ju - cu;
             const RayDir d = ray_dir(G, up, vp);
-            const float wa = d.ax ? d.wy : d.wx;
-            const float wb = d.ax ? d.wx : d.wy;
-            const float rinv = __frcp_rn(wa);
-            const float rb = wb * rinv, rz = d.wz * rinv;
+            const int ia = d.ax, ib = 1 - d.ax;
+            const DF wa = df_affine(G.Wc[ia], G.Wc_lo[ia], G.Eu[ia], G.Eu_lo[ia], G.Ev[ia], G.Ev_lo[ia], up, vp);
+            const DF wb = df_affine(G.Wc[ib], G.Wc_lo[ib], G.Eu[ib], G.Eu_lo[ib], G.Ev[ib], G.Ev_lo[ib], up, vp);
+            const DF wz = df_affine(G.Wc[2], G.Wc_lo[2], G.Eu[2], G.Eu_lo[2], G.Ev[2], G.Ev_lo[2], up, vp);
             const float *N = d.ax ? G.NY : G.NX;
+            const float *Nl = d.ax ? G.NY_lo : G.NX_lo;
+            const DF nb = df_affine(N[0], Nl[0], N[1], Nl[1], N[2], Nl[2], up, vp);
+            const DF nz = df_affine(N[3], Nl[3], N[4], Nl[4], N[5], Nl[5], up, vp);
+            const DF rb = df_div(wb, wa), rz = df_div(wz, wa);
             // centred crossing of this ray with the voxel's plane, minus the voxel
             const float ca = d.ax ? cy : cx, cb = d.ax ? cx : cy;
-            const float pb = fmaf(vp, N[2], fmaf(up, N[1], N[0])) * rinv;
-            const float pz = fmaf(vp, N[5], fmaf(up, N[4], N[3])) * rinv;
-            const float eb = fmaf(ca, rb, pb) - cb;
-            const float ez = fmaf(ca, rz, pz) - cz;
+            const DF xb = df_add(df_div(nb, wa), df_mul_f(rb, ca));
+            const DF xz = df_add(df_div(nz, wa), df_mul_f(rz, ca));
+            const float eb = __fadd_rn(__fsub_rn(xb.hi, cb), xb.lo);
+            const float ez = __fadd_rn(__fsub_rn(xz.hi, cz), xz.lo);
             const float hb = 1.0f - fabsf(eb);
             const float hz = 1.0f - fabsf(ez);
             if (hb > 0.0f && hz > 0.0f) {
                 float w = hb * hz;
-                if (!WEIGHTED) w *= sqrtf(fmaf(rz, rz, fmaf(rb, rb, 1.0f))) * a.h;
+                if (!WEIGHTED) w *= sqrtf(fmaf(rz.hi, rz.hi, fmaf(rb.hi, rb.hi, 1.0f))) * a.h;
                 SinoLoad<NCH, ST>::add(sino_view, (size_t)jv * a.nu + ju, w, acc);
             }
         }
@@ -173,10 +183,11 @@ __device__ __forceinline__ void bp_view_sep(const ViewGeom &G, const float4 *__r
     }
 }
 
-template <typename ST>
+// NF: floats of each table staged (VG_HI: the float32 part; 64: all of it)
+template <typename ST, int NF = VG_HI>
 __device__ __forceinline__ void stage_views(ViewGeom *Gs, const BPArgs &a, int c0, int cn, int tid, int nthreads) {
-    for (int t = tid; t < cn * VG_HI; t += nthreads) {
-        const int vi = t / VG_HI, e = t % VG_HI;
+    for (int t = tid; t < cn * NF; t += nthreads) {
+        const int vi = t / NF, e = t % NF;
         reinterpret_cast<float *>(&Gs[vi])[e] =
             __ldg(reinterpret_cast<const float *>(a.views + a.view0 + (c0 + vi) * a.stride) + e);
     }
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
     for (int c0 = 0; c0 < a.nviews; c0 += BP_CHUNK) {
         const int cn = min(BP_CHUNK, a.nviews - c0);
         __syncthreads();
-        stage_views<ST>(Gs, a, c0, cn, tid, BP_BX * BP_BY * BP_BZ);
+        stage_views<ST, sizeof(ViewGeom) / 4>(Gs, a, c0, cn, tid, BP_BX * BP_BY * BP_BZ);
         __syncthreads();
         if (active) {
             for (int vi = 0; vi < cn; ++vi)
@@ -300,7 +311,13 @@ __global__ void __launch_bounds__(BS_THREADS)
     __shared__ float acc[NCH][ROWS][BS_THREADS];
     const int tid = threadIdx.x;
     const int jx = blockIdx.x * BS_TX + (tid % BS_TX), jy = blockIdx.y * BS_TY + tid / BS_TX;
-    const int z0 = blockIdx.z * Z;
+    // blockIdx.z = split * (z-slabs) + slab; split s takes views [i0, i1)
+    // and writes partial volume s of `out`
+    const int zblocks = gridDim.z / a.splits;
+    const int split = blockIdx.z / zblocks;
+    const int z0 = (blockIdx.z - split * zblocks) * Z;
+    const int per = (a.nviews + a.splits - 1) / a.splits;
+    const int i0 = split * per, i1 = min(a.nviews, i0 + per);
 #pragma unroll
     for (int q = 0; q < NCH; ++q)
         for (int r = 0; r < ROWS; ++r) acc[q][r][tid] = 0.0f;
@@ -310,7 +327,7 @@ __global__ void __launch_bounds__(BS_THREADS)
         const float cx = (float)jx - ic, cy = (float)jy - ic;
         const float zlo = (float)z0 - 1.0f, zhi = (float)(z0 + Z);  // crossings that touch the slab
         const size_t view_elems = (size_t)a.nu * a.nv;
-        for (int i = 0; i < a.nviews; ++i) {
+        for (int i = i0; i < i1; ++i) {
             const int k = a.view0 + i * a.stride;
             const float *G = reinterpret_cast<const float *>(a.views + k);
             // projected u range of the voxel column (the cube bound; z-free without tilt)
@@ -408,6 +425,7 @@ __global__ void __launch_bounds__(BS_THREADS)
             }
         }
         const size_t nvox = (size_t)a.n * a.n * a.n;
+        float *o = out + (size_t)split * NCH * nvox;
         for (int zz = 0; zz < Z; ++zz) {
             const int z = z0 + zz;
             if (z >= a.n) break;
@@ -415,8 +433,8 @@ __global__ void __launch_bounds__(BS_THREADS)
 #pragma unroll
             for (int q = 0; q < NCH; ++q) {
                 float v = acc[q][zz + 2][tid];
-                if (accumulate) v += out[idx + q * nvox];
-                out[idx + q * nvox] = v;
+                if (accumulate) v += o[idx + q * nvox];
+                o[idx + q * nvox] = v;
             }
         }
     }
@@ -468,11 +486,42 @@ __global__ void k_column_table_df(const ViewGeom *__restrict__ views, int K, int
     o[3] = make_float4(e1c.lo, 0.0f, 0.0f, 0.0f);
 }
 
+// out = (accumulate ? out : 0) + sum over s of part[s], in order of s.
+__global__ void k_sum_splits(size_t len, int splits, const float *__restrict__ part, float *__restrict__ out,
+                             int accumulate) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x) {
+        float v = accumulate ? out[i] : 0.0f;
+        for (int q = 0; q < splits; ++q) v += __ldg(part + (size_t)q * len + i);
+        out[i] = v;
+    }
+}
+
+// Number of view ranges for a slab launch of `blocks` blocks: about one wave
+// of resident blocks in all (coarse grids and OS-EMTR subsets otherwise fill
+// a fraction of the SMs), at most what `cap` floats of partial volumes hold.
+template <typename KF>
+int slab_splits(KF kernel, int blocks, int nviews, size_t vol_floats, size_t cap) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BS_THREADS, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int sp = (sms * occ + blocks / 2) / blocks;
+    if (sp > 16) sp = 16;
+    if (sp > nviews) sp = nviews;
+    if ((size_t)sp * vol_floats > cap) sp = (int)(cap / vol_floats);
+    return sp < 1 ? 1 : sp;
+}
+
 // NCH = 2 writes channel c to out + c * n^3.  WEIGHTED: the sinogram carries
-// each ray's dl already (internal solver path).
+// each ray's dl already (internal solver path).  split_buf (cap floats, or
+// NULL): scratch for partial volumes, with which an under-filled slab launch
+// splits its views into ranges summed afterwards in a fixed order.
 template <int NCH, typename ST, bool WEIGHTED = false>
 int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int stride, const ST *sino,
-                       float *out, int accumulate, cudaStream_t s) {
+                       float *out, int accumulate, cudaStream_t s, float *split_buf = nullptr, size_t cap = 0) {
     const LevelInfo &L = g->lev[level];
     BPArgs a;
     a.views = L.d_views;
@@ -483,11 +532,25 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
     a.view0 = view0;
     a.stride = stride;
     a.nviews = nviews;
+    a.splits = 1;
     if (g->separable && WEIGHTED && L.d_cols) {
         constexpr int Z = SlabCfg<NCH>::Z;
         dim3 grid((L.n + BS_TX - 1) / BS_TX, (L.n + BS_TY - 1) / BS_TY, (L.n + Z - 1) / Z);
-        MGCT_KERNEL(KK_BACKPROJECT, s,
-                    k_backproject_slab<NCH, ST><<<grid, BS_THREADS, 0, s>>>(a, L.d_cols, sino, out, accumulate));
+        const size_t vol_floats = (size_t)NCH * L.n * L.n * L.n;
+        if (split_buf && nviews > 1)
+            a.splits = slab_splits(k_backproject_slab<NCH, ST>, (int)(grid.x * grid.y * grid.z), nviews, vol_floats,
+                                   cap);
+        if (a.splits == 1) {
+            MGCT_KERNEL(KK_BACKPROJECT, s,
+                        k_backproject_slab<NCH, ST><<<grid, BS_THREADS, 0, s>>>(a, L.d_cols, sino, out, accumulate));
+        } else {
+            grid.z *= a.splits;
+            MGCT_KERNEL(KK_BACKPROJECT, s,
+                        k_backproject_slab<NCH, ST><<<grid, BS_THREADS, 0, s>>>(a, L.d_cols, sino, split_buf, 0));
+            const int sb = (int)((vol_floats + 255) / 256 < 4096 ? (vol_floats + 255) / 256 : 4096);
+            MGCT_KERNEL(KK_BACKPROJECT, s,
+                        k_sum_splits<<<sb, 256, 0, s>>>(vol_floats, a.splits, split_buf, out, accumulate));
+        }
     } else if (g->separable) {
         const int zper = BP_BZ * BPS_ZB;
         dim3 grid((L.n + BP_BX - 1) / BP_BX, (L.n + BP_BY - 1) / BP_BY, (L.n + zper - 1) / zper);
@@ -545,6 +608,7 @@ int launch_backproject_public(const mgct_geom *g, int level, int view0, int nvie
     a.nv = L.nv;
     a.h = (float)L.h;
     a.stride = stride;
+    a.splits = 1;
     constexpr int Z = SlabCfg<1>::Z;
     const dim3 grid((L.n + BS_TX - 1) / BS_TX, (L.n + BS_TY - 1) / BS_TY, (L.n + Z - 1) / Z);
     for (int c0 = 0; c0 < nviews; c0 += (int)chunk) {

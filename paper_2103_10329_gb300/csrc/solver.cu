@@ -193,7 +193,9 @@ static int lw_direction(const mgct_geom *g, int level, const float *mu, const fl
     MGCT_TRY(project_quads<ST>(g, level, mu, w.muT, w.quads, er, s, &nb));
     (void)nv3;
     MGCT_TRY(launch_sum_partials(w.part, nb, 1, w.sums + 0, s));
-    MGCT_TRY(launch_backproject<1, ST, true>(g, level, 0, K, 1, r, w.grad, 0, s));
+    // the quads are free until the line search: room for partial volumes
+    MGCT_TRY(launch_backproject<1, ST, true>(g, level, 0, K, 1, r, w.grad, 0, s, reinterpret_cast<float *>(w.quads),
+                                             2 * quad_elems(L.n) * 4));
     *d_out = w.grad;
     if (o.precondition) {
         MGCT_TRY(launch_precondition(L.n, g->desc.p_slice_axis, w.grad, w.d, s, g->has_pkernel ? g->pkernel : nullptr));
@@ -299,7 +301,11 @@ static int osemtr(const mgct_geom *g, int level, int M, float *mu, const float *
         MGCT_TRY(launch_transpose_xy<float>(L.n, mu, w.muT, s));
         EpiEMTerms e{w.c2, b, pi, L.nu, L.nv, cnt};
         MGCT_TRY(launch_project<float>(g, level, m, cnt, M, mu, w.muT, e, s));
-        MGCT_TRY(launch_backproject<2, float2, true>(g, level, m, cnt, M, w.c2, w.nd, 0, s));
+        // c2 holds room for every view; past this subset's views it is free
+        const size_t used = (size_t)cnt * L.nu * L.nv;
+        MGCT_TRY(launch_backproject<2, float2, true>(g, level, m, cnt, M, w.c2, w.nd, 0, s,
+                                                     reinterpret_cast<float *>(w.c2 + used),
+                                                     2 * (sino_elems(g, L) - used)));
         MGCT_TRY(launch_em_update(nv3, mu, w.nd, w.part, s));
     }
     return MGCT_OK;

@@ -313,10 +313,11 @@ __global__ void __launch_bounds__(BS_THREADS)
     const int jx = blockIdx.x * BS_TX + (tid % BS_TX), jy = blockIdx.y * BS_TY + tid / BS_TX;
     // blockIdx.z = split * (z-slabs) + slab; split s takes views [i0, i1)
     // and writes partial volume s of `out`
-    const int zblocks = gridDim.z / a.splits;
+    const int splits = DFA ? 1 : a.splits;  // the public form never splits
+    const int zblocks = gridDim.z / splits;
     const int split = blockIdx.z / zblocks;
     const int z0 = (blockIdx.z - split * zblocks) * Z;
-    const int per = (a.nviews + a.splits - 1) / a.splits;
+    const int per = (a.nviews + splits - 1) / splits;
     const int i0 = split * per, i1 = min(a.nviews, i0 + per);
 #pragma unroll
     for (int q = 0; q < NCH; ++q)
@@ -496,9 +497,11 @@ __global__ void k_sum_splits(size_t len, int splits, const float *__restrict__ p
     }
 }
 
-// Number of view ranges for a slab launch of `blocks` blocks: about one wave
-// of resident blocks in all (coarse grids and OS-EMTR subsets otherwise fill
-// a fraction of the SMs), at most what `cap` floats of partial volumes hold.
+// Number of view ranges for a slab launch of `blocks` blocks: enough for
+// about four waves of resident blocks in all, as grid 0 has (coarse grids and
+// OS-EMTR subsets otherwise fill a fraction of the SMs, and a launch of one
+// or two waves loses its tail), at most 16 and what `cap` floats of partial
+// volumes hold.
 template <typename KF>
 int slab_splits(KF kernel, int blocks, int nviews, size_t vol_floats, size_t cap) {
     int dev = 0, sms = 0, occ = 0;
@@ -508,7 +511,7 @@ int slab_splits(KF kernel, int blocks, int nviews, size_t vol_floats, size_t cap
         cudaGetLastError();
         return 1;
     }
-    int sp = (sms * occ + blocks / 2) / blocks;
+    int sp = (4 * sms * occ + blocks - 1) / blocks;
     if (sp > 16) sp = 16;
     if (sp > nviews) sp = nviews;
     if ((size_t)sp * vol_floats > cap) sp = (int)(cap / vol_floats);

@@ -51,3 +51,31 @@ def test_ray_voxel_rates_positive():
     t_ray, t_vox = bench._ray_voxel_rates(og, vol, 200, sino_views=3)
     assert np.isfinite(t_ray) and t_ray > 0
     assert np.isfinite(t_vox) and t_vox > 0
+
+
+def test_count_nnz_matches_the_oracle_matrix():
+    """The roofline's work count: bench.count_nnz counts, per ray, the major-
+    axis planes whose sample lies within one voxel of the volume (so at least
+    one bilinear tap is nonzero), times 4 taps.  At 8^3 the planes must be
+    exactly those that hold a nonzero entry of the oracle's A, assembled
+    column by column from A e_j."""
+    n, nu, k = 8, 12, 3
+    scan = _scan(n, nu, k)
+    g = O.level_geometry(scan, 0)
+    cols = []
+    for j in range(n ** 3):
+        e = np.zeros(n ** 3)
+        e[j] = 1.0
+        cols.append(O.project(g, e.reshape(n, n, n)).ravel())
+    a = np.stack(cols, axis=1)  # rays x voxels, voxel j = (iz * n + iy) * n + ix
+    iz, iy, ix = np.unravel_index(np.arange(n ** 3), (n, n, n))
+    planes = 0
+    for r in range(a.shape[0]):
+        kv, ju = divmod(r, nu)
+        kk, jv = divmod(kv, nu)
+        w = g.det[kk] + ju * g.pu[kk] + jv * g.pv[kk] - g.src[kk]
+        coord = iy if abs(w[1]) > abs(w[0]) else ix
+        planes += len(np.unique(coord[a[r] != 0.0]))
+    got = bench.count_nnz(scan.theta, scan.z, scan.pitch, n, nu, nu, device="cpu")
+    assert planes > k * nu * nu  # most rays cross several planes
+    assert got == 4.0 * planes

@@ -931,7 +931,18 @@ def gpu_arm(args, rank, world):
         cpu = {"value": gups, "unit": "GUPS", "cores": thr, "kind": "oracle",
                "sample": f"FP64 oracle A and A^T at grid 0 on {cnt} of {K} views ({t:.1f} s)"}
         if not args.no_beside and args.workload == "c2":
-            beside = oracle_beside((cnt, ta, tat, vol_np), (g, b), full_c2=args.oracle_full)
+            # a side measurement: its failure (say, too little free device
+            # memory for the 1024^3 calls) is reported, not fatal to the line
+            try:
+                beside = oracle_beside((cnt, ta, tat, vol_np), (g, b), full_c2=args.oracle_full)
+            except Exception as ex:  # noqa: BLE001
+                import torch
+                beside = {"error": f"{type(ex).__name__}: {ex}"[:300]}
+                try:
+                    torch.cuda.synchronize()
+                    torch.cuda.empty_cache()
+                except Exception:  # noqa: BLE001
+                    pass
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": world, "steps": args.steps,

@@ -777,6 +777,17 @@ def gpu_arm(args, rank, world):
                          "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_clock:.0f} MHz"},
                 "hbm": {"bytes_alg": hbm_b, "frac_of_measured": hbm_b / t_s / 1e9 / peaks.get("hbm_gbs", 6790.0),
                         "ncu_bytes_per_launch": tr["bytes_per_launch"] if tr else None}}
+        # the on-chip peaks measured by the library's microbenchmarks, beside
+        # the derived ones the fraction uses
+        try:
+            mp = mgct.measure_onchip_peaks()
+            roof["measured_onchip"] = {
+                "fp32_tflops": mp["fp32_tflops"], "lds_gbs": mp["lds_gbs"],
+                "how": "mgct_measure_onchip_peaks: independent FMA chains; conflict-free 16-byte shared loads",
+                "gather_frac_of_measured_lds": gather_b / t_s / 1e9 / mp["lds_gbs"],
+                "fp32_frac_of_measured": fl / t_s / 1e12 / mp["fp32_tflops"]}
+        except Exception as ex:  # noqa: BLE001
+            roof["measured_onchip"] = {"error": f"{type(ex).__name__}: {ex}"[:200]}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None}

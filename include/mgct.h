@@ -409,6 +409,14 @@ uint64_t mgct_launch_count(int reset);
  * up as designed.  Returns MGCT_OK (the device context stays usable). */
 int mgct_check_bounded_wait(double seconds, int *expired, mgct_stream stream);
 
+/* Measures the two on-chip peaks the projector and back-projector are held
+ * against (the paper has no counterpart): *fp32_tflops, the FP32 rate of
+ * independent FMA chains (2 flop each) on every SM, and *lds_gbs, the rate
+ * of conflict-free 16-byte shared-memory loads (the L1 data path), each the
+ * median of five CUDA-event-timed launches on `stream` after one untimed
+ * launch.  Allocates nothing; synchronises `stream`.  A few milliseconds. */
+int mgct_measure_onchip_peaks(double *fp32_tflops, double *lds_gbs, mgct_stream stream);
+
 /* Kernel trace (tracing subsystem; the paper has none).  mgct_trace_enable(1)
  * clears the record and starts recording a CUDA event pair on the launching
  * stream around every kernel the library issues; 0 stops and clears.

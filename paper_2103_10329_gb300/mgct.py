@@ -59,7 +59,9 @@ def lib():
     L.mgct_geometry_set_preconditioner.argtypes = [vp, vp]
     L.mgct_bilateral.argtypes = [i, vp, vp, d, d, i, vp]
     L.mgct_check_bounded_wait.argtypes = [d, vp, vp]
-    for fn in ("mgct_geometry_set_preconditioner", "mgct_bilateral", "mgct_check_bounded_wait"):
+    L.mgct_measure_onchip_peaks.argtypes = [vp, vp, vp]
+    for fn in ("mgct_geometry_set_preconditioner", "mgct_bilateral", "mgct_check_bounded_wait",
+               "mgct_measure_onchip_peaks"):
         getattr(L, fn).restype = ctypes.c_int
     L.mgct_geometry_destroy.argtypes = [vp]
     L.mgct_geometry_destroy.restype = None
@@ -137,6 +139,15 @@ def check_bounded_wait(seconds: float = 0.2) -> bool:
     flag = ctypes.c_int(0)
     _check(L.mgct_check_bounded_wait(float(seconds), ctypes.byref(flag), _stream()))
     return flag.value == 1
+
+
+def measure_onchip_peaks() -> dict:
+    """The FP32 FMA rate (TFLOP/s) and the shared-memory load bandwidth (GB/s)
+    of the current device, measured by the library (mgct_measure_onchip_peaks)."""
+    L = lib()
+    fp32, lds = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(L.mgct_measure_onchip_peaks(ctypes.byref(fp32), ctypes.byref(lds), _stream()))
+    return {"fp32_tflops": fp32.value, "lds_gbs": lds.value}
 
 
 TRACE_KINDS = ("project", "backproject", "precondition", "transpose", "grid", "update", "reduce",

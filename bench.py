@@ -485,7 +485,7 @@ def oracle_beside(c2_sample, c2_gpu, full_c2=False, samples=100000):
     # --- 512^3: oracle on a sample of views, GPU whole calls
     n, nu, K = 512, 768, 1440
     vol = synth.random_volume(n, SEED)
-    gups, t, cnt, _, s_a, s_at = oracle_sample(None, target_s=8.0, vol=vol, dims=(n, nu, K))
+    _, _, cnt, _, s_a, s_at = oracle_sample(None, target_s=8.0, vol=vol, dims=(n, nu, K))
     ta, tat = s_a * K / cnt, s_at * K / cnt
     scan, th, z = scan_of(n, nu, K)
     og = O.level_geometry(scan, 0)
@@ -500,7 +500,7 @@ def oracle_beside(c2_sample, c2_gpu, full_c2=False, samples=100000):
         "ray_voxel_extrapolation_check": {"A_s": r_ray * K * nu * nu, "AT_s": r_vox * n ** 3 * K}}
     nnz3, ta3, tat3 = K * nu * nu * n, ta, tat
 
-    # --- 1024^3: oracle extrapolated from random rays and voxels
+    # --- 1024^3: oracle extrapolated by its per-nonzero rate at 512^3; GPU whole calls
     n, nu, K = 1024, 1536, 2880
     scan, th, z = scan_of(n, nu, K)
     og = O.level_geometry(scan, 0)

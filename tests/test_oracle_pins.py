@@ -394,6 +394,81 @@ def test_osemtr_fixed_point_and_direction():
     assert r1 < 0.5 * r0
 
 
+def _dense_from_weights(g):
+    """A as a dense matrix from the per-entry weight function alone (rows
+    (view, v, u), columns (z, y, x)), independent of the projector's loops."""
+    n = g.n
+    A = np.zeros((g.n_views * g.nv * g.nu, n ** 3))
+    for k in range(g.n_views):
+        for jv in range(g.nv):
+            for ju in range(g.nu):
+                row = (k * g.nv + jv) * g.nu + ju
+                for iz in range(n):
+                    for iy in range(n):
+                        for ix in range(n):
+                            A[row, (iz * n + iy) * n + ix] = O.weight(g, k, ju, jv, ix, iy, iz)
+    return A
+
+
+@pytest.mark.parametrize("m_sub", [1, 3])
+def test_osemtr_pass_brute_force(m_sub):
+    """Eq. 3 written out with a dense A from the per-entry weights at 5^3,
+    subset by subset (views k = m mod M, in order m = 0..M-1):
+    mu += A_m^T (exp(-A_m mu) - exp(-b_m)) / A_m^T (exp(-A_m mu) A_m 1),
+    where the denominator exceeds 1e-12 of its maximum; the oracle's pass
+    (projector and scatter loops) must agree to 1e-12."""
+    n, k = 5, 6
+    scan = make_scan(n, nviews=k, seed=21, nu=8, nv=8)
+    g = O.level_geometry(scan, 0)
+    A = _dense_from_weights(g)
+    x = 0.6 * synth.random_volume(n, 22) + 0.1
+    b = (A @ x.ravel()) * 1.05 + 0.01
+    mu0 = 0.5 * synth.random_volume(n, 23) + 0.2
+    got = O.osemtr_pass(g, mu0, b.reshape(k, g.nv, g.nu), n_subsets=m_sub)
+    mu = mu0.ravel().copy()
+    rows_per_view = g.nv * g.nu
+    for m in range(m_sub):
+        rows = np.concatenate([np.arange(v * rows_per_view, (v + 1) * rows_per_view) for v in range(m, k, m_sub)])
+        Am = A[rows]
+        t = np.exp(-(Am @ mu))
+        num = Am.T @ (t - np.exp(-b[rows]))
+        den = Am.T @ (t * (Am @ np.ones(n ** 3)))
+        mask = den > 1e-12 * den.max()
+        mu[mask] += num[mask] / den[mask]
+    assert np.abs(mu - mu0.ravel()).max() > 1e-3  # the pass moved mu
+    np.testing.assert_allclose(got.ravel(), mu, rtol=0, atol=1e-12)
+
+
+def test_landweber_step_brute_force():
+    """Eq. 4 written out with the dense A at 5^3 and Eq. 5 as a dense 27-point
+    operator: d = p (A^T (b - A mu)), alpha = <r, A d> / |A d|^2,
+    mu + alpha d; the oracle's step must agree to 1e-12."""
+    n, k = 5, 5
+    scan = make_scan(n, nviews=k, seed=24, nu=8, nv=8)
+    g = O.level_geometry(scan, 0)
+    A = _dense_from_weights(g)
+    mu0 = synth.random_volume(n, 25)
+    b = A @ synth.random_volume(n, 26).ravel()
+    got, st = O.landweber_step(g, mu0, b.reshape(k, g.nv, g.nu))
+    kern = O.eq5_kernel(2)
+    P = np.zeros((n ** 3, n ** 3))
+    for iz in range(n):
+        for iy in range(n):
+            for ix in range(n):
+                for dz in (-1, 0, 1):
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            z, y, x = iz + dz, iy + dy, ix + dx
+                            if 0 <= z < n and 0 <= y < n and 0 <= x < n:
+                                P[(iz * n + iy) * n + ix, (z * n + y) * n + x] = kern[dz + 1, dy + 1, dx + 1]
+    r = b - A @ mu0.ravel()
+    d = P @ (A.T @ r)
+    ad = A @ d
+    alpha = float(r @ ad) / float(ad @ ad)
+    assert abs(st["alpha"] - alpha) <= 1e-12 * abs(alpha)
+    np.testing.assert_allclose(got.ravel(), mu0.ravel() + alpha * d, rtol=0, atol=1e-12)
+
+
 def test_multigrid_single_level_is_one_landweber_step():
     n = 8
     scan = make_scan(n, nviews=6, seed=12)

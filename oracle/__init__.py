@@ -502,9 +502,10 @@ def multigrid(scan: Scan, mu: np.ndarray, b_levels, levels: int, level: int = 0,
     b_g being this grid's own data (`b`, else b_levels[level]): a variant
     that is not in the paper (Brandt's FAS coarse equation), under which an
     exact solution of the fine problem is a fixed point of the iteration.
-    parity unpinned beyond L = 1 for the plain recursion (no closed form):
-    checked against the paper's qualitative claim and against the GPU; the FAS
-    form is pinned by its fixed point.  bilateral = (sigma_s, sigma_r, radius)
+    The plain recursion has no closed form; it is pinned at 8^3 with two and
+    three grids against the same reading of Alg. 1 written out with dense
+    operators (A from the per-entry weights), and checked against the paper's
+    qualitative claim; the FAS form is pinned by its fixed point.  bilateral = (sigma_s, sigma_r, radius)
     applies Alg. 1's BilateralFilter after each grid's Landweber step and soft
     threshold (None: not applied)."""
     g = level_geometry(scan, level)

@@ -450,17 +450,7 @@ def test_landweber_step_brute_force():
     mu0 = synth.random_volume(n, 25)
     b = A @ synth.random_volume(n, 26).ravel()
     got, st = O.landweber_step(g, mu0, b.reshape(k, g.nv, g.nu))
-    kern = O.eq5_kernel(2)
-    P = np.zeros((n ** 3, n ** 3))
-    for iz in range(n):
-        for iy in range(n):
-            for ix in range(n):
-                for dz in (-1, 0, 1):
-                    for dy in (-1, 0, 1):
-                        for dx in (-1, 0, 1):
-                            z, y, x = iz + dz, iy + dy, ix + dx
-                            if 0 <= z < n and 0 <= y < n and 0 <= x < n:
-                                P[(iz * n + iy) * n + ix, (z * n + y) * n + x] = kern[dz + 1, dy + 1, dx + 1]
+    P = _dense_eq5(n)
     r = b - A @ mu0.ravel()
     d = P @ (A.T @ r)
     ad = A @ d
@@ -495,6 +485,109 @@ def test_multigrid_structure_two_levels():
     mc2 = O.osemtr_pass(O.level_geometry(scan, 1), mc, bl[1])
     want, _ = O.landweber_step(O.level_geometry(scan, 0), mu0 + O.prolong(mc2 - mc), b)
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+def _dense_eq5(n):
+    """Eq. 5 (z slices) as a dense n^3 x n^3 correlation with zero padding."""
+    kern = O.eq5_kernel(2)
+    P = np.zeros((n ** 3, n ** 3))
+    for iz in range(n):
+        for iy in range(n):
+            for ix in range(n):
+                for dz in (-1, 0, 1):
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            z, y, x = iz + dz, iy + dy, ix + dx
+                            if 0 <= z < n and 0 <= y < n and 0 <= x < n:
+                                P[(iz * n + iy) * n + ix, (z * n + y) * n + x] = kern[dz + 1, dy + 1, dx + 1]
+    return P
+
+
+def _dense_prolong_1d(nc):
+    """Cell-centred linear interpolation to 2 nc cells: fine cell f sits at
+    coarse coordinate f/2 - 1/4, between its two nearest coarse centres
+    (weights 3/4 and 1/4), the outer neighbour clamped at the edges."""
+    M = np.zeros((2 * nc, nc))
+    for f in range(2 * nc):
+        i, near = divmod(f, 2)
+        other = min(max(i + (1 if near else -1), 0), nc - 1)
+        M[f, i] += 0.75
+        M[f, other] += 0.25
+    return M
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_multigrid_brute_force(levels):
+    """Two iterations of Alg. 1 written out with dense operators at 8^3 (grids
+    8, 4 and 2): A per grid from the per-entry weights, restriction as 2x2x2
+    and 2x2 means, prolongation as the Kronecker product of the 1-D cell-
+    centred interpolation, Eq. 5 as a dense stencil, OS-EMTR on the coarsest
+    grid (8 subsets, one view each) and the line-searched Landweber step on
+    every other grid.  The oracle's multigrid must agree to 1e-11."""
+    n, k = 8, 8
+    scan = make_scan(n, nviews=k, seed=27, nu=12, nv=12)
+    A = [_dense_from_weights(O.level_geometry(scan, l)) for l in range(levels)]
+    sizes = [(n >> l, 12 >> l) for l in range(levels)]
+
+    def restrict_vol(m):
+        R = np.zeros((m ** 3 // 8, m ** 3))
+        h = m // 2
+        for z in range(m):
+            for y in range(m):
+                for x in range(m):
+                    R[((z // 2) * h + y // 2) * h + x // 2, (z * m + y) * m + x] = 1.0 / 8
+        return R
+
+    def restrict_sino(d):
+        R = np.zeros((k * (d // 2) ** 2, k * d * d))
+        h = d // 2
+        for v in range(k):
+            for jv in range(d):
+                for ju in range(d):
+                    R[(v * h + jv // 2) * h + ju // 2, (v * d + jv) * d + ju] = 0.25
+        return R
+
+    def landweber(l, mu, b):
+        P = _dense_eq5(sizes[l][0])
+        r = b - A[l] @ mu
+        dd = P @ (A[l].T @ r)
+        ad = A[l] @ dd
+        den = float(ad @ ad)
+        return mu + (float(r @ ad) / den if den > 0 else 0.0) * dd
+
+    def osemtr(l, mu, b):
+        mu = mu.copy()
+        rows_per_view = sizes[l][1] ** 2
+        pi = A[l] @ np.ones(A[l].shape[1])
+        for m in range(8):
+            rows = np.arange(m * rows_per_view, (m + 1) * rows_per_view)
+            Am = A[l][rows]
+            t = np.exp(-(Am @ mu))
+            num = Am.T @ (t - np.exp(-b[rows]))
+            den = Am.T @ (t * pi[rows])
+            mask = den > 1e-12 * den.max()
+            mu[mask] += num[mask] / den[mask]
+        return mu
+
+    x = synth.random_volume(n, 28)
+    b = [A[0] @ x.ravel()]
+    for l in range(1, levels):
+        b.append(restrict_sino(sizes[l - 1][1]) @ b[-1])
+
+    def mg(l, mu):
+        if l + 1 < levels:
+            mc = restrict_vol(sizes[l][0]) @ mu
+            mc_new = mg(l + 1, mc) if l + 1 < levels - 1 else osemtr(l + 1, mc, b[l + 1])
+            p1 = _dense_prolong_1d(sizes[l + 1][0])
+            mu = mu + np.kron(np.kron(p1, p1), p1) @ (mc_new - mc)
+        return landweber(l, mu, b[l])
+
+    mu = np.zeros(n ** 3)
+    for _ in range(2):
+        mu = mg(0, mu)
+    got = O.reconstruct(scan, b[0].reshape(k, 12, 12), iters=2, levels=levels)
+    assert np.abs(mu).max() > 0.1
+    np.testing.assert_allclose(got.ravel(), mu, rtol=0, atol=1e-11)
 
 
 def test_precondition_custom_kernel():

@@ -516,14 +516,15 @@ def _dense_prolong_1d(nc):
     return M
 
 
-@pytest.mark.parametrize("levels", [2, 3])
-def test_multigrid_brute_force(levels):
+@pytest.mark.parametrize("levels,fas", [(2, False), (3, False), (3, True)])
+def test_multigrid_brute_force(levels, fas):
     """Two iterations of Alg. 1 written out with dense operators at 8^3 (grids
     8, 4 and 2): A per grid from the per-entry weights, restriction as 2x2x2
     and 2x2 means, prolongation as the Kronecker product of the 1-D cell-
     centred interpolation, Eq. 5 as a dense stencil, OS-EMTR on the coarsest
     grid (8 subsets, one view each) and the line-searched Landweber step on
-    every other grid.  The oracle's multigrid must agree to 1e-11."""
+    every other grid.  With fas the coarse data are R (b - A mu) + A_c R mu
+    instead of R b.  The oracle's multigrid must agree to 1e-11."""
     n, k = 8, 8
     scan = make_scan(n, nviews=k, seed=27, nu=12, nv=12)
     A = [_dense_from_weights(O.level_geometry(scan, l)) for l in range(levels)]
@@ -574,18 +575,19 @@ def test_multigrid_brute_force(levels):
     for l in range(1, levels):
         b.append(restrict_sino(sizes[l - 1][1]) @ b[-1])
 
-    def mg(l, mu):
+    def mg(l, mu, bl):
         if l + 1 < levels:
             mc = restrict_vol(sizes[l][0]) @ mu
-            mc_new = mg(l + 1, mc) if l + 1 < levels - 1 else osemtr(l + 1, mc, b[l + 1])
+            bc = restrict_sino(sizes[l][1]) @ (bl - A[l] @ mu) + A[l + 1] @ mc if fas else b[l + 1]
+            mc_new = mg(l + 1, mc, bc) if l + 1 < levels - 1 else osemtr(l + 1, mc, bc)
             p1 = _dense_prolong_1d(sizes[l + 1][0])
             mu = mu + np.kron(np.kron(p1, p1), p1) @ (mc_new - mc)
-        return landweber(l, mu, b[l])
+        return landweber(l, mu, bl)
 
     mu = np.zeros(n ** 3)
     for _ in range(2):
-        mu = mg(0, mu)
-    got = O.reconstruct(scan, b[0].reshape(k, 12, 12), iters=2, levels=levels)
+        mu = mg(0, mu, b[0])
+    got = O.reconstruct(scan, b[0].reshape(k, 12, 12), iters=2, levels=levels, fas=fas)
     assert np.abs(mu).max() > 0.1
     np.testing.assert_allclose(got.ravel(), mu, rtol=0, atol=1e-11)
 

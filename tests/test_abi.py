@@ -63,3 +63,7 @@ def test_host_side_argument_checks(L):
     flag = ctypes.c_int(0)
     assert L.mgct_check_bounded_wait(0.0, ctypes.byref(flag), None) == -1
     assert L.mgct_check_bounded_wait(0.1, None, None) == -1
+    L.mgct_measure_onchip_peaks.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    x = ctypes.c_double(0.0)
+    assert L.mgct_measure_onchip_peaks(None, ctypes.byref(x), None) == -1
+    assert L.mgct_measure_onchip_peaks(ctypes.byref(x), None, None) == -1

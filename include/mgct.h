@@ -373,14 +373,20 @@ int mgct_landweber_learned(const mgct_geom *geom, int level, float *vol, const f
  * allocator, or a process with a device-memory budget fixed at start-up.
  * Instead of the handle's scratch it uses one static device array inside the
  * library, mgct_project_residual_static_bytes() bytes (about 10 MiB), which
- * every GPU that loads the library holds until the process exits.  Limits:
+ * every GPU that loads the library's device code holds until the process
+ * exits.  With lazy module loading (the CUDA default) that memory is taken
+ * when the device code is first used on a device, at the latest by the first
+ * call of this entry point there: a caller whose device-memory budget is
+ * fixed later should make one warm-up call at start-up.  Limits:
  * at most 128^3 voxels on the chosen grid and at most 262144 projector
  * blocks (ceil(nu_g/32) * ceil(nv_g/8) * nviews, with nviews rounded up to a
  * multiple of 32 above 32 views); larger requests fail with
  * MGCT_ESHAPE and a message naming the limit.  It calls no cudaMalloc,
- * cudaFree or other allocating routine.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * cudaFree or other allocating routine.  The first call in a device's
+ * context looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current and keeps it for that context (a context created anew,
+ * e.g. after cudaDeviceReset, gets its own lookup); make that first call
+ * before any stream capture.  All calls share
  * the one array, so calls that overlap on the GPU (different streams, or
  * different host threads, without ordering between them) race on it and give
  * wrong results; the array keeps the last call's contents, and every word a

@@ -9,8 +9,13 @@
 // a process whose device-memory budget is fixed at start-up -- can still run
 // the projector with its residual norm, passing only inputs and outputs.
 //
-// The array is part of the library image: every GPU that loads libmgct holds
-// it (NOALLOC_BYTES) until the process exits, whether or not it is used.
+// The array is part of the library's device module: every GPU on which the
+// module is loaded holds it (NOALLOC_BYTES) until the process exits, whether
+// or not it is used.  Under lazy module loading (the CUDA default) the module,
+// and with it the array, is loaded on the first use of the library's device
+// code on that device -- at the latest by this entry point's first call, whose
+// cudaGetSymbolAddress loads it.  A caller whose device-memory budget is fixed
+// later should make one call (any size within the limits) at start-up.
 #include <mutex>
 
 #include "common.cuh"
@@ -32,19 +37,55 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void *g_addr[MAX_DEVICES] = {};
+unsigned long long g_ctx[MAX_DEVICES] = {};  // id of the context the address belongs to
 
-// Device address of the scratch on the current device, looked up on the
-// first call made with that device current.
+// Identity of the calling thread's current context (cuCtxGetCurrent +
+// cuCtxGetId, reached through the runtime's driver entry points so that the
+// library needs no link against libcuda); 0 when the driver cannot say.
+unsigned long long current_context_id() {
+    typedef int (*get_current_t)(void **);
+    typedef int (*get_id_t)(void *, unsigned long long *);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2) {
+            get_current = reinterpret_cast<get_current_t>(f1);
+            get_id = reinterpret_cast<get_id_t>(f2);
+        } else {
+            cudaGetLastError();
+        }
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch in the current device's current context.
+// It is looked up (cudaGetSymbolAddress) on the first call made in a context
+// and cached under that context's id; a context created anew on the same
+// device (after cudaDeviceReset, or a released and re-created primary
+// context) loads the module again, so its address is looked up again.  When
+// the context's id cannot be read (no context is current on this thread yet,
+// or the driver lacks the call) the address is looked up on that call.
 int scratch_address(void **out) {
     int dev = 0;
     MGCT_TRY(check_cuda(cudaGetDevice(&dev), "cudaGetDevice"));
     if (dev < 0 || dev >= MAX_DEVICES) return set_error(MGCT_EINVAL, "device ordinal out of range");
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (!g_addr[dev] || ctx == 0 || g_ctx[dev] != ctx) {
         void *p = nullptr;
         MGCT_TRY(check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(static scratch)"));
         if (!p) return set_error(MGCT_ECUDA, "cudaGetSymbolAddress returned NULL");
         g_addr[dev] = p;
+        g_ctx[dev] = ctx;
     }
     *out = g_addr[dev];
     return MGCT_OK;

@@ -7,7 +7,7 @@ import torch
 
 import oracle as O
 from paper_2103_10329_gb300 import synth
-from tests.helpers import cuda, gpu_geom, oracle_scan, scan_desc, to_np
+from tests.helpers import TOL_F32, check_err, cuda, gpu_geom, oracle_scan, rel_err, scan_desc, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -17,6 +17,21 @@ def built():
     from paper_2103_10329_gb300 import build
     build.build()
     O.build()
+
+
+# Geometry-gradient bound, per parameter type relative to that type's
+# largest entry.  A view's gradient sums r_ray * dA_ray/dphi over its rays in
+# float64, each ray's derivative summed along the ray in float32 from the
+# bilinear gradient at the sample (a difference of neighbouring voxels).
+# Float32 rounding of each term (~6e-8) and the sample positions' error
+# (~1e-6 voxel, times the second difference of the smooth test volumes) give
+# each ray's derivative a relative error e_ray ~ 1e-6; the sum over R rays
+# of signed residuals cancels to ~sqrt(R) of a typical term while the errors
+# add like sqrt(R) too, but with the full term size rather than the signed
+# one, so the ratio is about e_ray * (rms |r D| / |mean r D|), up to ~1e2 for
+# near-zero views of a type: 1e-4 of the type's largest entry.  The
+# measured maxima are recorded beside it (MGCT_PARITY_REPORT).
+GRAD_TOL = 1e-4
 
 
 def smooth_volume(n, seed=5):
@@ -37,10 +52,9 @@ def test_geometry_grad_vs_oracle(tilt):
     ref = O.geometry_grad(oracle_scan(d), vol.astype(np.float32).astype(np.float64),
                           y.astype(np.float32).astype(np.float64))
     got = to_np(mgct.geometry_grad(g, cuda(vol), cuda(y)))
-    err = np.abs(got - ref)
     # per parameter type, relative to that type's largest entry
     for j in range(5):
-        assert err[:, j].max() <= 2e-4 * np.abs(ref[:, j]).max(), (j, err[:, j].max(), np.abs(ref[:, j]).max())
+        check_err(np.abs(got[:, j] - ref[:, j]) / np.abs(ref[:, j]).max(), GRAD_TOL)
 
 
 def test_view_subset_gradient():
@@ -72,16 +86,20 @@ def test_autograd_project_matches_oracle():
     ref_vol = O.backproject(og, y_np.astype(np.float64))
     ref_phi = O.geometry_grad(oracle_scan(d), vol_np.astype(np.float32).astype(np.float64), y_np.astype(np.float64))
     gv = to_np(vol.grad)
-    assert np.abs(gv - ref_vol).max() <= 1e-5 * np.abs(ref_vol).max() * 10
+    # A^T of a signed sinogram: per voxel, relative to A^T |y| (the scale of
+    # the sum's rounding error), as every back-projection test measures it
+    ref_abs = O.backproject(og, np.abs(y_np).astype(np.float64))
+    den = np.maximum(ref_abs, 1e-2 * ref_abs.max())
+    check_err(np.abs(gv - ref_vol) / den, TOL_F32)
     gp = phi.grad.cpu().numpy()
     for j in range(5):
-        assert np.abs(gp[:, j] - ref_phi[:, j]).max() <= 2e-4 * np.abs(ref_phi[:, j]).max()
+        check_err(np.abs(gp[:, j] - ref_phi[:, j]) / np.abs(ref_phi[:, j]).max(), GRAD_TOL)
     # the backward of the back-projection is the projection
     yy = cuda(y_np).requires_grad_(True)
     w = cuda(vol_np)
     (AG.backproject(yy, g) * w).sum().backward()
     ref_y = O.project(og, vol_np.astype(np.float32).astype(np.float64))
-    assert np.abs(to_np(yy.grad) - ref_y).max() <= 1e-5 * np.abs(ref_y).max() * 10
+    check_err(rel_err(to_np(yy.grad), ref_y), TOL_F32)
 
 
 def test_joint_estimation_recovers_detector_offset():
@@ -149,5 +167,4 @@ def test_geometry_grad_full_size_sampled():
     ds = dict(d, theta=d["theta"][views], z=d["z"][views], drift=drift[views])
     ref = O.geometry_grad(oracle_scan(ds), vol.astype(np.float64), to_np(y[torch.as_tensor(views, device="cuda")]))
     for j in range(5):
-        scale = np.abs(ref[:, j]).max()
-        assert np.abs(got[views, j] - ref[:, j]).max() <= 2e-4 * scale, (j, got[views, j], ref[:, j])
+        check_err(np.abs(got[views, j] - ref[:, j]) / np.abs(ref[:, j]).max(), GRAD_TOL)

@@ -73,3 +73,41 @@ def test_static_scratch_rejects_oversized_requests(L):
     assert _static_call(L, g, 1, 0, 4, 1, vol1, out1, torch.zeros_like(out1), ss) == 0
     torch.cuda.synchronize()
     assert L.mgct_project_residual_static_bytes() > 8 * 2 ** 20
+
+
+def test_static_scratch_calls_allocate_no_device_memory(L):
+    """The property callers rely on: once the library is loaded on the device
+    (one warm-up call), further calls of any size within the limits change
+    neither the device's free memory nor torch's allocator statistics."""
+    from paper_2103_10329_gb300 import mgct
+    d = scan_desc(64, 96, 96, 90, 2105, levels=2)
+    g = gpu_geom(d)
+    calls = []
+    for level, v0, cnt, stride, seed in [(0, 0, 90, 1, 7), (1, 2, 20, 4, 8), (0, 5, 33, 2, 9)]:
+        n, nu, nv, _, _ = g.level(level)
+        vol = cuda(synth.random_volume(n, seed))
+        b = cuda(np.random.default_rng(seed).random((cnt, nv, nu)) + 0.5)
+        out = torch.empty((cnt, nv, nu), device="cuda")
+        ss = torch.empty((1,), dtype=torch.float64, device="cuda")
+        ref_ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ref = mgct.project(g, vol, level=level, views=(v0, cnt, stride), b=b, sumsq=ref_ss)
+        calls.append((level, v0, cnt, stride, vol, out, b, ss, ref, ref_ss))
+    # warm-up: the first call in this context may load the module (and its array)
+    c = calls[0]
+    assert _static_call(L, g, *c[:8]) == 0, L.mgct_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(2):
+        for c in calls:
+            assert _static_call(L, g, *c[:8]) == 0, L.mgct_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0, (free0, free1)
+    for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
+    for level, v0, cnt, stride, vol, out, b, ss, ref, ref_ss in calls:
+        e = rel_err(to_np(out), to_np(ref))
+        assert e.max() <= TOL_F32, summary(e)
+        assert abs(ss.item() - ref_ss.item()) <= 1e-9 * ref_ss.item()

@@ -245,6 +245,25 @@ inline size_t project_blocks(int nu, int nv, int nviews) {
     const size_t vg = nviews < PJ_VG ? nviews : PJ_VG;
     return (size_t)((nu + PJ_BX - 1) / PJ_BX) * vg * groups * ((nv + PJ_BY - 1) / PJ_BY);
 }
+// Column projector (tilt-free geometries): a block is PC_COLS detector
+// columns (one warp each) by PC_ROWS rows (one lane each).
+constexpr int PC_COLS = 8;
+constexpr int PC_ROWS = 32;
+#ifndef MGCT_PC_VG
+#define MGCT_PC_VG 32
+#endif
+constexpr int PC_VG = MGCT_PC_VG;  // views per block group (column projector)
+inline size_t project_blocks_col(int nu, int nv, int nviews) {
+    if (nviews <= 0) return 0;
+    const size_t groups = (size_t)(nviews + PC_VG - 1) / PC_VG;
+    const size_t vg = nviews < PC_VG ? nviews : PC_VG;
+    return (size_t)((nu + PC_COLS - 1) / PC_COLS) * vg * groups * ((nv + PC_ROWS - 1) / PC_ROWS);
+}
+// Blocks of either projector: the size of per-block partial-sum buffers.
+inline size_t project_blocks_any(int nu, int nv, int nviews) {
+    const size_t a = project_blocks(nu, nv, nviews), b = project_blocks_col(nu, nv, nviews);
+    return a > b ? a : b;
+}
 
 // ---------------------------------------------------------------------------
 // Internal kernels used across translation units (host launchers)
@@ -258,6 +277,15 @@ __host__ __device__ inline size_t quad_elems(int n) { return (size_t)quad_side(n
 // packed 16-bit pairs for bf16 / fp16) [z + QD_PAD][i][b + QD_PAD]
 template <typename T, typename SRC = float>
 int launch_build_quads(int n, const SRC *src, void *dst, cudaStream_t s);
+// z-fastest quad copies for the column projector: src [z][i][b] ->
+// dst[i][b + QD_PAD][z + QD_PAD], each entry the footprint as two z pairs
+// (V(jz, jb), V(jz + 1, jb)), (V(jz, jb + 1), V(jz + 1, jb + 1))
+template <typename T, typename SRC = float>
+int launch_build_zquads(int n, const SRC *src, void *dst, cudaStream_t s);
+// float32 z-fastest pairs for the column projector: (V(jz, jb), V(jz, jb + 1))
+// at dst[i][jb + QD_PAD][jz + QD_PAD], zero outside the volume
+template <typename SRC = float>
+int launch_build_zpairs(int n, const SRC *src, void *dst, cudaStream_t s);
 template <typename T>
 int launch_transpose_xy(int n, const T *in, T *out, cudaStream_t s);
 

@@ -314,8 +314,8 @@ int mgct_geometry_create(const mgct_geom_desc *d, mgct_geom **out) {
         return st;
     }
     size_t nvox = (size_t)d->n * d->n * d->n;
-    // partials: one per projector block (32 x 8 pixels per view), two values each
-    size_t blocks = project_blocks(d->nu, d->nv, K);
+    // partials: one per projector block (either projector's tiling), two values each
+    size_t blocks = project_blocks_any(d->nu, d->nv, K);
     size_t vblocks = (nvox + 255) / 256;
     size_t gblocks = 5 * (size_t)K * ((d->nu + PJ_BX - 1) / PJ_BX);  // geometry-gradient partials
     g->scratch_part_count = 2 * (blocks > vblocks ? blocks : vblocks) + 64;

@@ -3,13 +3,20 @@
 // The projection operator P of Eq. 1 (Sec. 2) is discretised by Joseph's
 // method: each ray is sampled at its crossings with the voxel-centre planes
 // normal to its major axis, by bilinear interpolation within the plane, and
-// each sample carries the path length between planes.  One thread per ray;
-// a warp covers 32 adjacent detector columns of one detector row of one view,
-// so at every plane the warp's taps fall on one or two contiguous rows of the
-// volume copy whose fastest axis is the in-plane horizontal axis:
-//   y-major rays sample plane y = i of vol  [z][y][x]  (taps along x, z)
-//   x-major rays sample plane x = i of volT [z][x][y]  (taps along y, z)
+// each sample carries the path length between planes.  One thread per ray,
+// in two kernels:
+//   k_project_col (tilt-free geometries, the solvers' and mgct_project's
+//     path): a warp takes 32 rows of one detector column, whose rays share
+//     their in-plane crossing, and reads z-fastest copies of the volume;
+//   k_project (any geometry): a warp covers 32 adjacent detector columns of
+//     one detector row, so at every plane its taps fall on one or two
+//     contiguous rows of the volume copy whose fastest axis is the in-plane
+//     horizontal axis.
+// Either way, y-major rays sample plane y = i of vol [z][y][x] (taps along x,
+// z) and x-major rays plane x = i of volT [z][x][y] (taps along y, z).
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -361,6 +368,259 @@ struct EpiEMTerms {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Column projector (tilt-free geometries).  The rays through one detector
+// column of a view lie in one vertical plane: they share their major axis,
+// they cross every plane i of that axis at the same in-plane coordinate
+//   b(c_a) = ic + pb + c_a rb                  (c_a = i - ic),
+// and their z crossings are affine in the row:
+//   z(c_a) = ic + e0(v') + c_a e1(v'),  e0 = ez0 + v' e10,  e1 = ezc + v' e1c,
+// with the column's quantities from the double-float column table.  A warp
+// takes 32 consecutive rows of one column.  The in-plane half of a sample is
+// then the same for the whole warp: the warp's lanes compute it for 32
+// planes at a time (in double-float, from the plane's own offset, so nothing
+// accumulates) into a small table in shared memory -- the fraction along b
+// and the offset of the (plane, b) row of entries -- that every lane reads
+// back with one broadcast load per sample.  Each lane steps its own z
+// crossing in 32.32 fixed point: exact integer additions, a step rounded to
+// 2^-32 voxel, so the position stays within ~1e-7 voxel over any number of
+// planes with no re-anchoring; the integer part is the entry index and the
+// fraction's top 23 bits become the float32 weight.
+//
+// The volume is read from z-fastest quads: entry (i, jb + QD_PAD, jz +
+// QD_PAD) holds (V(jz, jb), V(jz + 1, jb), V(jz, jb + 1), V(jz + 1, jb + 1))
+// at plane i, so the warp's 32 loads at one plane fall on one run of
+// consecutive entries and the two b-rows of a footprint are float pairs
+// along z (interpolated in b by one packed multiply-add).
+//
+// The warp walks the union of its rays' plane ranges.  A ray outside its own
+// range lies beyond the top or bottom face there (the in-plane clip is the
+// warp's), so its crossing's z index, clamped into the padded array, reads an
+// all-zero entry; planes past the union (the last batch) read the zero entry
+// row (plane 0, corner b = n + 1).  The clamp is exact, not a guard band.
+// ---------------------------------------------------------------------------
+#ifndef MGCT_PC_BATCH
+#define MGCT_PC_BATCH 8
+#endif
+constexpr int PC_BATCH = MGCT_PC_BATCH;  // plane loads in flight per ray
+constexpr int PC_TAB = 32;               // planes per table refill (one per lane)
+
+template <typename E>
+__device__ __forceinline__ float2 quad_pair(const E &Q, int which);
+template <>
+__device__ __forceinline__ float2 quad_pair<float4>(const float4 &Q, int which) {
+    return which ? make_float2(Q.z, Q.w) : make_float2(Q.x, Q.y);
+}
+
+// d = a * b + c and d = a - b on float pairs (one packed instruction each)
+__device__ __forceinline__ float2 fma_f2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub_f2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// Sample of one z-fastest quad: b-lerp of both z rows (packed), then z-lerp.
+template <typename VT>
+__device__ __forceinline__ float zquad_sample(const typename VolTraits<VT>::elem &Q, float2 tb2, float tz) {
+    float2 r0, r1;
+    if constexpr (std::is_same<typename VolTraits<VT>::elem, float4>::value) {
+        r0 = make_float2(Q.x, Q.y);
+        r1 = make_float2(Q.z, Q.w);
+    } else {
+        r0 = unpack2(Q.x, typename VolTraits<VT>::half_t());
+        r1 = unpack2(Q.y, typename VolTraits<VT>::half_t());
+    }
+    const float2 a = fma_f2(tb2, sub_f2(r1, r0), r0);  // values at jz, jz + 1
+    return fmaf(tz, a.y - a.x, a.x);
+}
+
+struct ColTab {
+    float tb, tb2, roff, pad;  // fraction along b (twice), row offset (int bits)
+};
+
+// Layouts of the column projector's z-fastest copies (entry (i, jb + QD_PAD,
+// jz + QD_PAD) of plane i):
+//   ZL_QUAD: the footprint as two z pairs, one 8-byte load a sample (16-bit
+//            storage);
+//   ZL_PAIR: (V(jz, jb), V(jz, jb + 1)) in float32, two 8-byte loads a
+//            sample (rows jz and jz + 1, adjacent in memory).
+// Measured at 256^3 / 720 views and 512^3 / 1440 views, float32 pairs took
+// 16.3 and 313 ms per projection, float32 quads (one 16-byte load, twice the
+// footprint) 18.2 and 415 ms, plain values (four 4-byte loads) 17.2 and
+// 315 ms: the pairs' footprint, twice the volume's, keeps the band of
+// planes that concurrently resident blocks read in L2.
+constexpr int ZL_QUAD = 0, ZL_PAIR = 1;
+template <typename VT, int LAYOUT>
+struct ZElem {
+    using type = typename VolTraits<VT>::elem;
+};
+template <typename VT>
+struct ZElem<VT, ZL_PAIR> {
+    using type = float2;
+};
+
+template <typename VT, int LAYOUT>
+__device__ __forceinline__ RaySum column_rays(const ProjArgs &a, const float4 *__restrict__ ct, int jv, bool row_ok,
+                                              const typename ZElem<VT, LAYOUT>::type *__restrict__ zqy,
+                                              const typename ZElem<VT, LAYOUT>::type *__restrict__ zqx,
+                                              ColTab *__restrict__ tab) {
+    using E = typename ZElem<VT, LAYOUT>::type;
+    // {ax, rb, rb_lo, pb}, {pb_lo, ez0, ez0_lo, ezc}, {ezc_lo, e10, e10_lo, e1c}, {e1c_lo, 0, 0, 0}
+    const float4 t0 = __ldg(ct), t1 = __ldg(ct + 1), t2 = __ldg(ct + 2), t3 = __ldg(ct + 3);
+    const DF rb{t0.y, t0.z}, pb{t0.w, t1.x}, ez0{t1.y, t1.z}, ezc{t1.w, t2.x}, e10{t2.y, t2.z}, e1c{t2.w, t3.x};
+    const E *__restrict__ base = t0.x != 0.0f ? zqy : zqx;
+    const int n = a.n, lane = threadIdx.x & 31;
+    const float ic = 0.5f * (float)(n - 1);
+    const float vp = (float)jv - 0.5f * (float)(a.nv - 1);
+    const DF e0 = df_add(ez0, df_mul_f(e10, vp));  // centred z crossing at the central plane
+    const DF e1 = df_add(ezc, df_mul_f(e1c, vp));  // its change per plane
+    const float rz = e1.hi;
+    const float dl_h = sqrtf(fmaf(rz, rz, fmaf(rb.hi, rb.hi, 1.0f)));
+    float lo = 0.0f, hi = (float)(n - 1);
+    clip_planes(pb.hi, rb.hi, ic, (float)n, lo, hi);
+    clip_planes(e0.hi, rz, ic, (float)n, lo, hi);
+    int i0 = 0x7fffffff, i1 = -1;
+    if (row_ok && lo <= hi) {
+        i0 = max(0, (int)floorf(lo));
+        i1 = min(n - 1, (int)ceilf(hi));
+    }
+    const int I0 = __reduce_min_sync(0xffffffffu, i0);
+    const int I1 = __reduce_max_sync(0xffffffffu, i1);
+    float acc = 0.0f;
+    if (I0 > I1) return RaySum{acc, dl_h * a.h};
+    const int side = quad_side(n);
+    // largest z (and b) entry index a sample may start at: corner n + 1 (an
+    // all-zero quad), or corner n where the sample reads index + 1 as well
+    const unsigned emax = (unsigned)side - (LAYOUT == ZL_QUAD ? 1u : 2u);
+    // z crossing at plane I0 as 32.32 fixed point, and its step per plane
+    int Iz;
+    float phiz;
+    split_coord(df_add(df_add(e0, df_mul_f(e1, __fsub_rn((float)I0, ic))), DF{ic, 0.0f}), Iz, phiz);
+    const unsigned zfrac = phiz < 1.0f ? (unsigned)__float2ull_rn(phiz * 4294967296.0f) : 0xffffffffu;
+    long long zpos = ((long long)Iz << 32) | (long long)zfrac;
+    const long long zstep = __float2ll_rn(e1.hi * 4294967296.0f) + __float2ll_rn(e1.lo * 4294967296.0f);
+    for (int c0 = I0; c0 <= I1; c0 += PC_TAB) {
+        // lane l: plane c0 + l of this warp's table
+        const int pc = c0 + lane;
+        float tbv = 0.0f;
+        int roff = (int)emax * side;  // plane 0, corner b = n + 1 (or n): zero entries
+        if (pc <= I1) {
+            int Ib;
+            float phib;
+            split_coord(df_add(df_add(pb, df_mul_f(rb, __fsub_rn((float)pc, ic))), DF{ic, 0.0f}), Ib, phib);
+            const unsigned bq = min((unsigned)(Ib + QD_PAD), emax);
+            roff = (pc * side + (int)bq) * side;
+            tbv = phib;
+        }
+        __syncwarp();
+        tab[lane] = ColTab{tbv, tbv, __int_as_float(roff), 0.0f};
+        __syncwarp();
+        const int cnt = min(PC_TAB, I1 - c0 + 1);
+        float part = 0.0f;
+        for (int kk = 0; kk < cnt; kk += PC_BATCH) {
+            constexpr int NL = LAYOUT == ZL_QUAD ? 1 : 2;
+            E Q[PC_BATCH][NL];
+            float2 tb[PC_BATCH];
+            float tz[PC_BATCH];
+#pragma unroll
+            for (int j = 0; j < PC_BATCH; ++j) {
+                const float4 te = reinterpret_cast<const float4 *>(tab)[kk + j];
+                tb[j] = make_float2(te.x, te.y);
+                const unsigned zlo = (unsigned)zpos;
+                const int zhi = (int)(zpos >> 32);
+                tz[j] = __uint_as_float(0x3f800000u | (zlo >> 9)) - 1.0f;
+                const unsigned zq = min((unsigned)(zhi + QD_PAD), emax);
+                const E *q = base + (unsigned)(__float_as_int(te.z) + (int)zq);
+                Q[j][0] = __ldg(q);
+                if constexpr (NL == 2) Q[j][1] = __ldg(q + 1);
+                zpos += zstep;
+            }
+#pragma unroll
+            for (int j = 0; j < PC_BATCH; ++j) {
+                if constexpr (LAYOUT == ZL_QUAD) {
+                    part += zquad_sample<VT>(Q[j][0], tb[j], tz[j]);
+                } else {
+                    const float a0 = fmaf(tb[j].x, Q[j][0].y - Q[j][0].x, Q[j][0].x);
+                    const float a1 = fmaf(tb[j].x, Q[j][1].y - Q[j][1].x, Q[j][1].x);
+                    part += fmaf(tz[j], a1 - a0, a0);
+                }
+            }
+        }
+        acc += part;
+        // the last batch stepped past the chunk: re-align the z position
+        zpos -= (long long)(((cnt + PC_BATCH - 1) / PC_BATCH) * PC_BATCH - cnt) * zstep;
+    }
+    return RaySum{acc, dl_h * a.h};
+}
+
+#ifndef MGCT_PC_MINB
+#define MGCT_PC_MINB 4
+#endif
+template <typename VT, int LAYOUT, typename Epi>
+__global__ void __launch_bounds__(PC_COLS *PC_ROWS, MGCT_PC_MINB)
+    k_project_col(ProjArgs a, const float4 *__restrict__ cols, const typename ZElem<VT, LAYOUT>::type *__restrict__ zqy,
+                  const typename ZElem<VT, LAYOUT>::type *__restrict__ zqx, Epi epi) {
+    __shared__ __align__(16) ColTab tab[PC_COLS][PC_TAB];
+    const int rtiles = (a.nv + PC_ROWS - 1) / PC_ROWS;
+    const int group = blockIdx.z / rtiles, rt = blockIdx.z - group * rtiles;
+    const int i = group * PC_VG + blockIdx.y;  // batch index
+    const bool view_ok = i < a.nviews;
+    const int k = a.view0 + (view_ok ? i : 0) * a.stride;
+    const int ju = blockIdx.x * PC_COLS + threadIdx.y;  // warp: one column
+    const int jv = rt * PC_ROWS + threadIdx.x;          // lane: one row
+    const bool active = view_ok && ju < a.nu && jv < a.nv;
+    RaySum rs{0.0f, 0.0f};
+    if (view_ok && ju < a.nu)  // uniform over the warp
+        rs = column_rays<VT, LAYOUT>(a, cols + ((size_t)k * a.nu + ju) * 4, jv, jv < a.nv, zqy, zqx,
+                                     tab[threadIdx.y]);
+    epi(i, k, jv, ju, active, rs.acc, rs.dlh);
+}
+
+template <typename VT, int LAYOUT, typename Epi>
+int launch_project_col(const mgct_geom *g, int level, int view0, int nviews, int stride,
+                       const typename ZElem<VT, LAYOUT>::type *zqy, const typename ZElem<VT, LAYOUT>::type *zqx,
+                       const Epi &epi, cudaStream_t s, int *nblocks = nullptr) {
+    const LevelInfo &L = g->lev[level];
+    ProjArgs a;
+    a.views = L.d_views;
+    a.n = L.n;
+    a.nu = L.nu;
+    a.nv = L.nv;
+    a.h = (float)L.h;
+    a.view0 = view0;
+    a.stride = stride;
+    a.nviews = nviews;
+    const int groups = (nviews + PC_VG - 1) / PC_VG;
+    const int vg = nviews < PC_VG ? nviews : PC_VG;
+    dim3 grid((L.nu + PC_COLS - 1) / PC_COLS, vg, groups * ((L.nv + PC_ROWS - 1) / PC_ROWS));
+    if (nblocks) *nblocks = (int)project_blocks_col(L.nu, L.nv, nviews);
+    if (nviews == 0) return MGCT_OK;
+    MGCT_KERNEL(KK_PROJECT, s,
+                k_project_col<VT, LAYOUT, Epi><<<grid, dim3(PC_ROWS, PC_COLS), 0, s>>>(a, L.d_cols_df, zqy, zqx, epi));
+    return MGCT_OK;
+}
+
+// The column projector applies where the geometry has no detector tilt (its
+// column table exists at every grid) and its entry offsets fit 31 bits
+// (volumes up to about 1290^3).
+inline bool use_column_projector(const mgct_geom *g, int level) {
+    const size_t n = g->lev[level].n, side = quad_side(g->lev[level].n);
+    return g->separable && g->lev[level].d_cols_df != nullptr && n * side * side < ((size_t)1 << 31);
+}
+
 template <typename VT, typename Epi>
 int launch_project(const mgct_geom *g, int level, int view0, int nviews, int stride,
                    const typename VolTraits<VT>::elem *vol, const typename VolTraits<VT>::elem *volT,
@@ -382,6 +642,36 @@ int launch_project(const mgct_geom *g, int level, int view0, int nviews, int str
     if (nviews == 0) return MGCT_OK;
     MGCT_KERNEL(KK_PROJECT, s, k_project<VT, Epi><<<grid, dim3(PJ_BX, PJ_BY), 0, s>>>(a, vol, volT, epi));
     return MGCT_OK;
+}
+
+// A over views [view0, view0 + nviews * stride) of volume v (type SRC), read
+// through quad copies of storage type ST: the transpose of v into vT, the
+// quads of both ray classes into `quads` (2 quad_elems(n) entries), then the
+// column projector (tilt-free geometries) or k_project with epilogue `e`.
+template <typename ST, typename SRC, typename Epi>
+int project_volume(const mgct_geom *g, int level, int view0, int nviews, int stride, const SRC *v, SRC *vT,
+                   void *quads, const Epi &e, cudaStream_t s, int *nb) {
+    using QE = typename VolTraits<Quad<ST>>::elem;
+    const LevelInfo &L = g->lev[level];
+    QE *q1 = static_cast<QE *>(quads);
+    QE *q2 = q1 + quad_elems(L.n);
+    MGCT_TRY(launch_transpose_xy<SRC>(L.n, v, vT, s));
+    if (use_column_projector(g, level)) {
+        if constexpr (std::is_same<ST, float>::value) {
+            float2 *z1 = static_cast<float2 *>(quads);
+            float2 *z2 = z1 + quad_elems(L.n);
+            MGCT_TRY((launch_build_zpairs<SRC>(L.n, v, z1, s)));
+            MGCT_TRY((launch_build_zpairs<SRC>(L.n, vT, z2, s)));
+            return launch_project_col<Quad<ST>, ZL_PAIR>(g, level, view0, nviews, stride, z1, z2, e, s, nb);
+        } else {
+            MGCT_TRY((launch_build_zquads<ST, SRC>(L.n, v, q1, s)));
+            MGCT_TRY((launch_build_zquads<ST, SRC>(L.n, vT, q2, s)));
+            return launch_project_col<Quad<ST>, ZL_QUAD>(g, level, view0, nviews, stride, q1, q2, e, s, nb);
+        }
+    }
+    MGCT_TRY((launch_build_quads<ST, SRC>(L.n, v, q1, s)));
+    MGCT_TRY((launch_build_quads<ST, SRC>(L.n, vT, q2, s)));
+    return launch_project<Quad<ST>>(g, level, view0, nviews, stride, q1, q2, e, s, nb);
 }
 
 }  // namespace mgct

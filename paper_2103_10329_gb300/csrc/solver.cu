@@ -65,7 +65,7 @@ static size_t sino_elems(const mgct_geom *g, const LevelInfo &L) {
     return (size_t)g->desc.n_views * L.nv * L.nu;
 }
 static size_t proj_blocks(const mgct_geom *g, const LevelInfo &L) {
-    return project_blocks(L.nu, L.nv, g->desc.n_views);
+    return project_blocks_any(L.nu, L.nv, g->desc.n_views);
 }
 
 struct LWSpace {
@@ -157,20 +157,13 @@ static int check_ws(const mgct_geom *g, int op, int level, const void *ws, size_
 // ---------------------------------------------------------------------------
 // Solver steps
 // ---------------------------------------------------------------------------
-// A v over every view through quad copies of v in storage type ST: the
-// transpose of v into `vT` (float32 scratch), the quads of both ray classes
-// into `quads`, then the projector with epilogue `e`.
+// A v over every view through quad copies of v in storage type ST (see
+// project_volume): vT is a float32 scratch volume, `quads` holds both ray
+// classes' copies.
 template <typename ST, typename Epi>
 static int project_quads(const mgct_geom *g, int level, const float *v, float *vT, float4 *quads, const Epi &e,
                          cudaStream_t s, int *nb) {
-    using QE = typename VolTraits<Quad<ST>>::elem;
-    const LevelInfo &L = g->lev[level];
-    QE *qy = reinterpret_cast<QE *>(quads);
-    QE *qx = qy + quad_elems(L.n);
-    MGCT_TRY(launch_transpose_xy<float>(L.n, v, vT, s));
-    MGCT_TRY(launch_build_quads<ST>(L.n, v, qy, s));
-    MGCT_TRY(launch_build_quads<ST>(L.n, vT, qx, s));
-    return launch_project<Quad<ST>>(g, level, 0, g->desc.n_views, 1, qy, qx, e, s, nb);
+    return project_volume<ST, float>(g, level, 0, g->desc.n_views, 1, v, vT, quads, e, s, nb);
 }
 
 // ST: storage type of the copies the projector and back-projector read (the
@@ -410,20 +403,14 @@ int mgct_project(const mgct_geom *g, int level, int view0, int nviews, int strid
     auto run = [&](auto vtag, auto otag) -> int {
         using VT = decltype(vtag);
         using OT = decltype(otag);
-        using QE = typename VolTraits<Quad<VT>>::elem;
         const VT *v = static_cast<const VT *>(vol);
         VT *vT = static_cast<VT *>(g->d_scratch_vol);
-        QE *qy = static_cast<QE *>(g->d_scratch_quads);
-        QE *qx = qy + quad_elems(L.n);
-        MGCT_TRY(launch_transpose_xy<VT>(L.n, v, vT, s));
-        MGCT_TRY((launch_build_quads<VT, VT>(L.n, v, qy, s)));
-        MGCT_TRY((launch_build_quads<VT, VT>(L.n, vT, qx, s)));
         if (b) {
             EpiResidual<OT> e{static_cast<OT *>(out), b, part, L.nu, L.nv, nviews};
-            return launch_project<Quad<VT>>(g, level, view0, nviews, stride, qy, qx, e, s, &nb);
+            return project_volume<VT, VT>(g, level, view0, nviews, stride, v, vT, g->d_scratch_quads, e, s, &nb);
         }
         EpiStore<OT> e{static_cast<OT *>(out), L.nu, L.nv};
-        return launch_project<Quad<VT>>(g, level, view0, nviews, stride, qy, qx, e, s, &nb);
+        return project_volume<VT, VT>(g, level, view0, nviews, stride, v, vT, g->d_scratch_quads, e, s, &nb);
     };
     auto run_v = [&](auto vtag) -> int {
         switch (ot) {
@@ -572,11 +559,15 @@ int mgct_multigrid_prepare(const mgct_geom *g, const float *b, void *ws, size_t 
         // PI = A 1 on the coarsest grid (Eq. 3: projected support length)
         int lc = g->levels - 1;
         const LevelInfo &C = g->lev[lc];
-        float *ones = m.mu[lc], *onesT = m.old[lc];
+        float *ones = m.mu[lc];
         MGCT_TRY(launch_fill(vox(C), ones, 1.0f, s));
-        MGCT_TRY(launch_fill(vox(C), onesT, 1.0f, s));
+        // the projector mgct_project runs, with the Landweber workspace's
+        // transpose and quads as scratch
+        Carver cw(m.lw_base);
+        LWSpace w = carve_lw(g, 0, cw);
         EpiStore<float> e{m.pi, C.nu, C.nv};
-        MGCT_TRY(launch_project<float>(g, lc, 0, K, 1, ones, onesT, e, s));
+        int nb = 0;
+        MGCT_TRY((project_volume<float, float>(g, lc, 0, K, 1, ones, w.muT, w.quads, e, s, &nb)));
     }
     return MGCT_OK;
 }

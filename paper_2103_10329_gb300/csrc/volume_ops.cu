@@ -91,6 +91,92 @@ template int launch_build_quads<__half, float>(int, const float *, void *, cudaS
 template int launch_build_quads<__nv_bfloat16, __nv_bfloat16>(int, const __nv_bfloat16 *, void *, cudaStream_t);
 template int launch_build_quads<__half, __half>(int, const __half *, void *, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// z-fastest quad copies (the column projector's input): dst[i][bq][zq] holds
+// the footprint of plane i at corner (jz, jb) = (zq, bq) - QD_PAD as two
+// pairs along z, (V(jz, jb), V(jz + 1, jb)) and (V(jz, jb + 1),
+// V(jz + 1, jb + 1)), zero outside the volume.  A block transposes one plane's (z, b) tile of src [z][i][b]
+// through shared memory: 33 x 33 source values (the tile and its +1
+// neighbours) read along b, entries written along z.
+// ---------------------------------------------------------------------------
+constexpr int ZQ_T = 32;
+template <typename T, typename QE, typename SRC>
+__global__ void __launch_bounds__(256) k_build_zquads(int n, const SRC *__restrict__ src, QE *__restrict__ dst) {
+    __shared__ float tile[ZQ_T + 1][ZQ_T + 1];  // [z][b], stride 33: conflict-free both ways
+    const int side = quad_side(n);
+    const int zq0 = blockIdx.x * ZQ_T, bq0 = blockIdx.y * ZQ_T, i = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r <= ZQ_T; r += 8) {
+        const int jz = zq0 + r - QD_PAD;
+        for (int c = tx; c <= ZQ_T; c += 32) {
+            const int jb = bq0 + c - QD_PAD;
+            tile[r][c] = ((unsigned)jz < (unsigned)n && (unsigned)jb < (unsigned)n)
+                             ? to_f32(__ldg(src + ((size_t)jz * n + i) * n + jb))
+                             : 0.0f;
+        }
+    }
+    __syncthreads();
+    const int zq = zq0 + tx;
+    if (zq >= side) return;
+    for (int c = ty; c < ZQ_T; c += 8) {
+        const int bq = bq0 + c;
+        if (bq >= side) break;
+        dst[((size_t)i * side + bq) * side + zq] =
+            make_quad(tile[tx][c], tile[tx + 1][c], tile[tx][c + 1], tile[tx + 1][c + 1], T());
+    }
+}
+
+template <typename T, typename SRC>
+int launch_build_zquads(int n, const SRC *src, void *dst, cudaStream_t s) {
+    using QE = typename std::conditional<std::is_same<T, float>::value, float4, uint2>::type;
+    const int side = quad_side(n);
+    dim3 grid((side + ZQ_T - 1) / ZQ_T, (side + ZQ_T - 1) / ZQ_T, n);
+    MGCT_KERNEL(KK_TRANSPOSE, s,
+                k_build_zquads<T, QE, SRC><<<grid, dim3(32, 8), 0, s>>>(n, src, static_cast<QE *>(dst)));
+    return MGCT_OK;
+}
+template int launch_build_zquads<float, float>(int, const float *, void *, cudaStream_t);
+template int launch_build_zquads<__nv_bfloat16, float>(int, const float *, void *, cudaStream_t);
+template int launch_build_zquads<__half, float>(int, const float *, void *, cudaStream_t);
+template int launch_build_zquads<__nv_bfloat16, __nv_bfloat16>(int, const __nv_bfloat16 *, void *, cudaStream_t);
+template int launch_build_zquads<__half, __half>(int, const __half *, void *, cudaStream_t);
+
+// float32 z-fastest pairs (V(jz, jb), V(jz, jb + 1)), same tiling
+template <typename SRC>
+__global__ void __launch_bounds__(256) k_build_zpairs(int n, const SRC *__restrict__ src, float2 *__restrict__ dst) {
+    __shared__ float tile[ZQ_T][ZQ_T + 1];  // [z][b]: the tile and the +1 neighbour along b
+    const int side = quad_side(n);
+    const int zq0 = blockIdx.x * ZQ_T, bq0 = blockIdx.y * ZQ_T, i = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < ZQ_T; r += 8) {
+        const int jz = zq0 + r - QD_PAD;
+        for (int c = tx; c <= ZQ_T; c += 32) {
+            const int jb = bq0 + c - QD_PAD;
+            tile[r][c] = ((unsigned)jz < (unsigned)n && (unsigned)jb < (unsigned)n)
+                             ? to_f32(__ldg(src + ((size_t)jz * n + i) * n + jb))
+                             : 0.0f;
+        }
+    }
+    __syncthreads();
+    const int zq = zq0 + tx;
+    if (zq >= side) return;
+    for (int c = ty; c < ZQ_T; c += 8) {
+        const int bq = bq0 + c;
+        if (bq >= side) break;
+        dst[((size_t)i * side + bq) * side + zq] = make_float2(tile[tx][c], tile[tx][c + 1]);
+    }
+}
+
+template <typename SRC>
+int launch_build_zpairs(int n, const SRC *src, void *dst, cudaStream_t s) {
+    const int side = quad_side(n);
+    dim3 grid((side + ZQ_T - 1) / ZQ_T, (side + ZQ_T - 1) / ZQ_T, n);
+    MGCT_KERNEL(KK_TRANSPOSE, s,
+                k_build_zpairs<SRC><<<grid, dim3(32, 8), 0, s>>>(n, src, static_cast<float2 *>(dst)));
+    return MGCT_OK;
+}
+template int launch_build_zpairs<float>(int, const float *, void *, cudaStream_t);
+
 
 // ---------------------------------------------------------------------------
 // Eq. 5 stencil: out = p * in, zero padding.  Block = 32 x 8 columns; each

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 from paper_2103_10329_gb300 import synth
-from tests.helpers import TOL_F32, cuda, gpu_geom, rel_err, scan_desc, summary, to_np
+from tests.helpers import TOL_F32, cuda, gpu_geom, scan_desc, summary, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +33,23 @@ def _static_call(L, g, level, view0, nviews, stride, vol, out, b, ss):
                                         ctypes.c_void_p(ss.data_ptr()),
                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     return st
+
+
+def _check_residual(out, ss, ref, ref_ss, b):
+    """The static path against mgct_project.  The two may run different
+    projector kernels (the static one reads the plain volume and its
+    transpose), each within the float32 per-ray tolerance of the oracle on
+    A mu, so their residuals b - A mu agree to TOL_F32 of A mu (not of the
+    residual, which may cancel) plus one float32 rounding step of the stored
+    difference (2^-23 |b|: the two may round b - A mu to neighbouring
+    floats), and their squared norms to 2 TOL_F32 sum |r| |A mu|."""
+    r, r_ref, bb = to_np(out), to_np(ref), to_np(b)
+    a_ref = bb - r_ref
+    den = TOL_F32 * np.maximum(np.abs(a_ref), 1e-2 * np.abs(a_ref).max()) + 2.0 ** -23 * np.abs(bb)
+    e = np.abs(r - r_ref) / den
+    assert e.max() <= 1.0, summary(e)
+    bound = 2 * TOL_F32 * float(np.sum(np.abs(r_ref) * np.abs(a_ref))) + 1e-12 * ref_ss.item()
+    assert abs(ss.item() - ref_ss.item()) <= bound, (ss.item(), ref_ss.item(), bound)
 
 
 def test_static_scratch_matches_allocating_path_twice(L):
@@ -53,9 +70,7 @@ def test_static_scratch_matches_allocating_path_twice(L):
         ss = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
         assert _static_call(L, g, level, v0, cnt, stride, vol, out, b, ss) == 0, L.mgct_last_error()
         torch.cuda.synchronize()
-        e = rel_err(to_np(out), to_np(ref))
-        assert e.max() <= TOL_F32, summary(e)
-        assert abs(ss.item() - ref_ss.item()) <= 1e-9 * ref_ss.item()
+        _check_residual(out, ss, ref, ref_ss, b)
 
 
 def test_static_scratch_rejects_oversized_requests(L):
@@ -108,6 +123,4 @@ def test_static_scratch_calls_allocate_no_device_memory(L):
     for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
         assert stats1.get(key, 0) == stats0.get(key, 0), key
     for level, v0, cnt, stride, vol, out, b, ss, ref, ref_ss in calls:
-        e = rel_err(to_np(out), to_np(ref))
-        assert e.max() <= TOL_F32, summary(e)
-        assert abs(ss.item() - ref_ss.item()) <= 1e-9 * ref_ss.item()
+        _check_residual(out, ss, ref, ref_ss, b)

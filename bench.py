@@ -5,15 +5,18 @@ GB300 (replicas only across GPUs).
 One step = one multigrid iteration of Alg. 1 at grid 0 (restrict, recurse,
 OS-EMTR on the coarsest grid, prolongate, and on every other grid one
 preconditioned Landweber step: A with residual, A^T, the Eq. 5 filter, a
-second A for the line search, the update).  Workload: 256^3 volume of 200
-random ellipsoids plus a porous texture, 384x384 detector, 720 views on the
-space-filling trajectory, 3 grids, Poisson noise at 1e4 photons per ray; the
-data are projected from a 2x finer phantom.
+second A for the line search, the update).
+
+Headline workload (the largest configuration): a 1024^3 volume of 100 random
+ellipsoids plus a porous texture, 1536x1536 detector, 2880 views on the
+space-filling trajectory, 4 grids, Poisson noise at 1e4 photons per ray.
+The 256^3 / 384^2 / 720-view workload (data projected from a 2x finer
+phantom) follows as a secondary line with the time-to-accuracy runs.
 
 The value is whole-job A+A^T throughput in GUPS: voxel-view updates (n_g^3 x
 views for every A and A^T call of the step, on every grid) per second.
-`--impl reference` times the FP64 CPU oracle (A and A^T on a sample of views)
-on the host cores instead.
+`--impl reference` times the FP64 CPU oracle (A and A^T on a sample of views
+and rows) on the host cores instead.
 """
 from __future__ import annotations
 
@@ -34,12 +37,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "A+A^T GUPS & % BW roofline; sec to RMSE≤1e-3 (learned/BF16 vs plain FP32)"
 WORKLOADS = {
-    # name: n, nu, views, levels, ellipsoids, axis range, texture, photons
+    # name: n, nu, views, levels, ellipsoids, axis range, texture, photons;
+    # fine: the data are projected from a phantom `fine` times finer (1: the
+    # reconstruction grid itself)
+    "c5": dict(n=1024, nu=1536, views=2880, levels=4, count=100, axis=(0.01, 0.08), texture=True,
+               photons=1e4, fine=1),
+    "c3": dict(n=512, nu=768, views=1440, levels=3, count=50, axis=(0.04, 0.2), texture=False, photons=0,
+               fine=2),
     "c2": dict(n=256, nu=384, views=720, levels=3, count=200, axis=(0.01, 0.08), texture=True,
-               photons=1e4),
-    "c1": dict(n=64, nu=96, views=90, levels=2, count=10, axis=(0.04, 0.2), texture=False, photons=0),
+               photons=1e4, fine=2),
+    "c1": dict(n=64, nu=96, views=90, levels=2, count=10, axis=(0.04, 0.2), texture=False, photons=0, fine=2),
     # half the views of c2, noise- and texture-free: the small case for ncu captures
-    "c2h": dict(n=256, nu=384, views=360, levels=3, count=50, axis=(0.01, 0.08), texture=False, photons=0),
+    "c2h": dict(n=256, nu=384, views=360, levels=3, count=50, axis=(0.01, 0.08), texture=False, photons=0,
+                fine=2),
 }
 SEED = 2103
 FP32_LANES_PER_SM, SMS = 128, 152
@@ -56,7 +66,9 @@ def workload_config(name):
     w = WORKLOADS[name]
     return {"workload": f"{w['n']}^3 volume, {w['count']} ellipsoids" + (" + porous texture" if w["texture"] else "")
             + f", {w['nu']}x{w['nu']} detector, {w['views']} space-filling views, {w['levels']} grids"
-            + (f", Poisson {w['photons']:.0e} photons/ray" if w["photons"] else ", noise-free"),
+            + (f", Poisson {w['photons']:.0e} photons/ray" if w["photons"] else ", noise-free")
+            + (", data projected from a 2x finer phantom" if w["fine"] == 2 else
+               ", data projected from the phantom on the reconstruction grid"),
             "n": w["n"], "detector": [w["nu"], w["nu"]], "views": w["views"], "levels": w["levels"],
             "iteration": "Alg. 1 multigrid, Landweber with line search, OS-EMTR M=8 on the coarsest grid",
             "l2": "inputs larger than L2 (sinogram %d MB)" % (w["views"] * w["nu"] ** 2 * 4 // 2 ** 20)}
@@ -200,14 +212,21 @@ def make_workload(name, device="cuda"):
     tex = synth.porous_texture(n, SEED + 3, device=device) if w["texture"] else None
     if tex is not None:
         truth += tex
-    # data from a phantom twice as fine (no inverse crime)
-    fine = synth.voxelize_ellipsoids(ph, 2 * n, supersample=1, device=device, dtype=torch.float32)
-    if tex is not None:
-        fine += tex.repeat_interleave(2, 0).repeat_interleave(2, 1).repeat_interleave(2, 2)
-    gf = mgct.Geometry(2 * n, nu, nu, th, z, pitch, levels=1)
-    b = mgct.project(gf, fine)
-    del fine
-    gf.close()
+    if w["fine"] == 2:
+        # data from a phantom twice as fine (no inverse crime)
+        fine = synth.voxelize_ellipsoids(ph, 2 * n, supersample=1, device=device, dtype=torch.float32)
+        if tex is not None:
+            fine += tex.repeat_interleave(2, 0).repeat_interleave(2, 1).repeat_interleave(2, 2)
+        gf = mgct.Geometry(2 * n, nu, nu, th, z, pitch, levels=1)
+        b = mgct.project(gf, fine)
+        del fine
+        gf.close()
+    else:
+        # at 1024^3 a 2048^3 phantom and its projector copies would take about
+        # 170 GB: the data come from the reconstruction grid's own phantom
+        gf = mgct.Geometry(n, nu, nu, th, z, pitch, levels=1)
+        b = mgct.project(gf, truth)
+        gf.close()
     if w["photons"]:
         b = synth.poisson_log_data(b, w["photons"], SEED + 2)
     torch.cuda.synchronize()
@@ -269,6 +288,8 @@ def oracle_sample(name, target_s=15.0, vol=None, views_cap=None, dims=None):
     g = O.level_geometry(scan, 0)
     if vol is None:
         vol = synth.random_volume(n, SEED)
+    if n >= 1024:
+        return _oracle_sample_rows(g, vol, K)
 
     def run(cnt):
         gs = g.subset(np.arange(cnt))
@@ -290,6 +311,34 @@ def oracle_sample(name, target_s=15.0, vol=None, views_cap=None, dims=None):
     return gups, t, cnt2, O.num_threads(), ta, tat
 
 
+ROW_SAMPLE = 16
+
+
+def _oracle_sample_rows(g, vol, K):
+    """The oracle at 1024^3, where its scatter A^T keeps one private FP64
+    volume per thread within 8 GB and so runs on one thread: A over one whole
+    view (all host threads), and A^T of that view on ROW_SAMPLE detector rows
+    spread evenly over it (a sub-detector of every (nv / ROW_SAMPLE)-th row),
+    scaled to the whole view by the row count.  Returns the tuple of
+    oracle_sample with the view's A and A^T seconds."""
+    import oracle as O
+    k = K // 2
+    gk = g.subset([k])
+    step = max(1, g.nv // ROW_SAMPLE)
+    r0 = (g.nv - step * (ROW_SAMPLE - 1)) // 2
+    band = O.LevelGeom(g.n, g.nu, ROW_SAMPLE, g.h, gk.src, gk.det + r0 * gk.pv, gk.pu, step * gk.pv)
+    t0 = time.perf_counter()
+    O.project(gk, vol)
+    t1 = time.perf_counter()
+    yb = O.project(band, vol)
+    t2 = time.perf_counter()
+    O.backproject(band, yb)
+    t3 = time.perf_counter()
+    ta, tat = t1 - t0, (t3 - t2) * g.nv / ROW_SAMPLE
+    gups = 2.0 * g.n ** 3 / (ta + tat) / 1e9
+    return gups, (t1 - t0) + (t3 - t2), 1, O.num_threads(), ta, tat
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -299,24 +348,29 @@ def reference_arm(args, rank):
     O.build()
     from paper_2103_10329_gb300 import synth
     vol = synth.random_volume(w["n"], SEED)
-    # one step = oracle A + A^T on a fixed sample of views
-    per_step_views = args.ref_views
+    # one step = oracle A + A^T on a fixed sample of views (at 1024^3: one
+    # view's A and A^T on a sample of its rows, scaled to the view)
+    per_step_views = args.ref_views if w["n"] < 1024 else 1
     vals = []
     for i in range(args.warmup + args.steps):
-        gups, t, cnt, thr, _, _ = oracle_sample(name, vol=vol, views_cap=per_step_views)
+        gups, t, cnt, thr, ta, tat = oracle_sample(name, vol=vol, views_cap=per_step_views)
         if i >= args.warmup:
-            vals.append((gups, t))
+            vals.append((gups, ta + tat))
     tot_t = sum(t for _, t in vals)
     units = 2.0 * w["n"] ** 3 * per_step_views * len(vals)
     value = units / tot_t / 1e9
+    sample = (f"FP64 oracle A and A^T at grid 0 on {per_step_views} of {w['views']} views per step"
+              if w["n"] < 1024 else
+              f"FP64 oracle per step: A over one of {w['views']} views (all threads) and its A^T on "
+              f"{ROW_SAMPLE} of {w['nu']} detector rows (one thread: 8 GB cap on the oracle's private "
+              f"volumes), scaled to the view")
     cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(name),
             "cpu_baseline": {"value": value, "unit": "GUPS", "cores": thr, "host_cores": cores, "kind": "oracle",
-                             "sample": f"FP64 oracle A and A^T at grid 0 on {per_step_views} of {w['views']} "
-                                       f"views per step"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -652,6 +706,235 @@ def hbm_kernel_rates(peak_gbs, n=512, reps=5):
             "kernels": out}
 
 
+def time_to_accuracy(args, W, rec, g, b, truth, vol):
+    """On the 256^3 / 720-view workload: PMGL vs SIRT at equal fine-grid
+    cost (FP32), full-resolution OS-EMTR, the 16-bit storage forms, the
+    learned correction (trained here), the BilateralFilter and PSF-kernel
+    forms against the plain FP32 two-iteration RMSE E2, and the literal
+    RMSE <= 1e-3 clock."""
+    import torch
+    from paper_2103_10329_gb300 import mgct
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+
+    def run_iters(storage, iters, net=None, bilateral=None):
+        v = torch.zeros_like(vol)
+        out = []
+        tot = 0.0
+        for _ in range(iters):
+            torch.cuda.synchronize()
+            s0.record()
+            if net is None:
+                rec.iterate(v, storage=storage, bilateral=bilateral)
+            else:
+                rec.iterate_learned(v, net, storage=storage)
+            s1.record()
+            torch.cuda.synchronize()
+            tot += s0.elapsed_time(s1)
+            out.append((tot, roi_rmse(v, truth)))
+        return out
+
+    base = run_iters(torch.float32, 2)
+    e2 = base[-1][1]
+    vs = torch.zeros_like(vol)
+    ws = mgct.workspace(g, mgct.WS_LANDWEBER, 0)
+    s0.record()
+    for _ in range(2):
+        mgct.landweber_step(g, vs, b, precond=False, ws=ws)
+    s1.record()
+    torch.cuda.synchronize()
+    tta = {"rmse_def": "RMS(mu - truth) / range(truth) over r <= 0.9R, |z| <= 0.9R",
+           "E2_pmgl_fp32_2iter": e2, "pmgl_fp32_2iter_ms": base[-1][0],
+           "sirt_2iter_ms": s0.elapsed_time(s1), "sirt_2iter_rmse_roi": roi_rmse(vs, truth),
+           "forms": {}}
+    # Fig. 2 analogue: OS-EMTR (Eq. 3, M = 8 subsets) at full resolution
+    del vs
+    ones = torch.ones_like(vol)
+    pi = mgct.project(g, ones)
+    del ones
+    we = mgct.workspace(g, mgct.WS_OSEMTR, 0)
+    ve = torch.zeros_like(vol)
+    em, tot = [], 0.0
+    for _ in range(10):
+        torch.cuda.synchronize()
+        s0.record()
+        mgct.osemtr_pass(g, ve, b, pi, n_subsets=8, ws=we)
+        s1.record()
+        torch.cuda.synchronize()
+        tot += s0.elapsed_time(s1)
+        em.append((tot, roi_rmse(ve, truth)))
+    tta["osemtr_full_res"] = {"subsets": 8, "per_pass_ms_cum": [e[0] for e in em],
+                              "per_pass_rmse_roi": [e[1] for e in em]}
+    del ve, we, pi
+    net = None
+    if not args.no_learned:
+        t0 = time.perf_counter()
+        net, train_info = train_correction(args.learn_phantoms, args.learn_steps)
+        train_info["wall_s"] = time.perf_counter() - t0
+        tta["learned_training"] = train_info
+    forms = [("fp32", torch.float32, False), ("bf16", torch.bfloat16, False), ("fp16", torch.float16, False)]
+    if net is not None:
+        forms += [("learned_fp32", torch.float32, True), ("learned_bf16", torch.bfloat16, True)]
+    # Alg. 1's BilateralFilter (no parameters in the paper): sigma_s = 1 voxel,
+    # sigma_r = 0.2, radius 1, the best of five settings tried on this workload
+    bil = (1.0, 0.2, 1)
+    forms += [("bilateral_fp32", torch.float32, "bil"), ("bilateral_bf16", torch.bfloat16, "bil")]
+    tta["bilateral"] = {"sigma_s_voxels": bil[0], "sigma_r": bil[1], "radius": bil[2],
+                        "chosen": "best of (1, 0.05, 1), (1, 0.1, 1), (1, 0.2, 1), (1.5, 0.1, 2), (0.8, 0.1, 1) "
+                                  "on this workload; E2 stays the plain form's"}
+    # a preconditioner fitted to the measured PSF of A^T A (in place of Eq. 5)
+    from paper_2103_10329_gb300 import psf as PSF
+    t0 = time.perf_counter()
+    kern, _ = PSF.derived_preconditioner(g)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    g.set_preconditioner(kern)
+    hist_psf = run_iters(torch.float32, 3)
+    g.set_preconditioner(None)
+    reach = next(((i + 1, t) for i, (t, e) in enumerate(hist_psf) if e <= e2 * (1 + 1e-3)), None)
+    tta["forms"]["psf_kernel_fp32"] = {"per_iter_ms_cum": [h[0] for h in hist_psf],
+                                       "per_iter_rmse_roi": [h[1] for h in hist_psf],
+                                       "iters_to_E2": reach[0] if reach else None,
+                                       "ms_to_E2": reach[1] if reach else None}
+    tta["psf_kernel"] = {"kernel_z0_plane": kern[1].tolist(), "kernel_z1_plane": kern[2].tolist(),
+                         "measure_and_fit_s": fit_s,
+                         "per_iter_ms_cum": [h[0] for h in hist_psf], "per_iter_rmse_roi": [h[1] for h in hist_psf]}
+    for name, st, use_net in forms:
+        if use_net == "bil":
+            hist = run_iters(st, 3, None, bil)
+        else:
+            hist = run_iters(st, 3, net if use_net else None)
+        reach = next(((i + 1, t) for i, (t, e) in enumerate(hist) if e <= e2 * (1 + 1e-3)), None)
+        tta["forms"][name] = {"per_iter_ms_cum": [h[0] for h in hist], "per_iter_rmse_roi": [h[1] for h in hist],
+                              "iters_to_E2": reach[0] if reach else None,
+                              "ms_to_E2": reach[1] if reach else None}
+    tta["E2_tolerance"] = "RMSE <= E2 (1 + 1e-3)"
+    if not args.no_literal:
+        tta["literal_rmse_1e-3"] = {
+            "c2": literal_tta(rec, g, truth, net),
+            "c1": literal_tta(None, None, None, net, workload="c1"),
+        }
+        rec.prepare(b)
+
+    return tta
+
+
+def family_rooflines(W, nnz, trace0, peaks, sm_clock, fp32_peak, mp=None):
+    """Roofline objects of the projector and back-projector families on the
+    finest grid: one grid-0 launch is one A (or A^T) over every view.  The
+    fraction is t_floor / t_launch with t_floor the largest of three floors
+    per launch:
+      HBM: one volume plus one sinogram at the measured copy bandwidth;
+      on-chip gather: 4 B per nonzero of A against the L1 at 128 B/clk/SM
+        (the binding floor of both families);
+      FP32: 2 flop per nonzero plus ~8 per sample against 128 lanes/SM.
+    `traffic` is the ncu DRAM bytes of the family's kernel recorded in
+    profiles/traffic.json, per launch: measured on its own workload, scaled
+    by the nonzeros from a smaller capture otherwise (stated in the object)."""
+    n, K, nu = W["n"], W["views"], W["nu"]
+    l1_peak = SMS * 128 * sm_clock * 1e6  # B/s
+    hbm_b = 4 * (n ** 3 + K * nu ** 2)
+    gather_b = 4 * nnz[0]
+    fl = 2 * nnz[0] + 8 * (nnz[0] / 4)
+    floors = {"hbm_ms": hbm_b / (peaks.get("hbm_gbs", 6790.0) * 1e9) * 1e3,
+              "onchip_gather_ms": gather_b / l1_peak * 1e3,
+              "fp32_ms": fl / (fp32_peak * 1e12) * 1e3}
+    names = {"project": "k_project_col", "backproject": "k_backproject_slab"}
+    out = {}
+    for fam, kname in names.items():
+        if fam not in trace0 or not trace0[fam][1]:
+            continue
+        t0_ms, t0_n = trace0[fam]
+        avg_ms = t0_ms / max(t0_n, 1)
+        t_s = avg_ms / 1e3
+        tr = traffic_record(kname)
+        traffic, tnote = None, None
+        if tr:
+            if tr.get("workload") == W["name"]:
+                traffic, tnote = tr["bytes_per_launch"], f"ncu capture of this workload ({tr['how']})"
+            elif tr.get("nnz_per_launch"):
+                traffic = tr["bytes_per_launch"] * nnz[0] / tr["nnz_per_launch"]
+                tnote = (f"scaled by nonzeros from the ncu capture at {tr.get('workload')} ({tr['how']}); "
+                         "L2 reuse falls at larger volumes, so the true figure is higher")
+        r = {"kernel": kname, "launches": "grid 0 (the finest grid)", "bound": "onchip-gather",
+             "binding_floor": "on-chip gather (L1, 4 B per nonzero of A), the largest of the three floors",
+             "achieved": gather_b / t_s / 1e9, "peak": l1_peak / 1e9, "unit": "GB/s",
+             "frac": gather_b / t_s / l1_peak,
+             "peak_source": f"derived: {SMS} SMs x 128 B/clk x {sm_clock:.0f} MHz of L1",
+             "def": "frac = t_floor / t_launch, t_floor = max(HBM, on-chip gather, FP32 floors); achieved = "
+                    "4 B per nonzero of A per launch / launch time",
+             "floors_ms": floors, "avg_launch_ms": avg_ms, "launches_timed": t0_n,
+             "work": f"{nnz[0]:.4g} nonzeros of A per launch (4 bilinear taps per in-volume sample)",
+             "traffic": traffic, "traffic_note": tnote,
+             "fp32": {"achieved_tflops": fl / t_s / 1e12, "peak_tflops": fp32_peak,
+                      "frac": fl / t_s / 1e12 / fp32_peak},
+             "hbm": {"bytes_alg": hbm_b, "frac_of_measured": hbm_b / t_s / 1e9 / peaks.get("hbm_gbs", 6790.0)}}
+        if mp:
+            r["measured_onchip"] = {"lds_gbs": mp["lds_gbs"], "fp32_tflops": mp["fp32_tflops"],
+                                    "gather_frac_of_measured_lds": gather_b / t_s / 1e9 / mp["lds_gbs"]}
+        out[kname] = r
+    return out
+
+
+def kernel_table(W, nnz, trace, steps):
+    """Per-family time, launches, share, algorithmic TFLOP/s and GUPS per step."""
+    n, K, L = W["n"], W["views"], W["levels"]
+    flops = {"project": 0.0, "backproject": 0.0}
+    for lv in range(L):
+        if L == 1 or lv < L - 1:
+            flops["project"] += 2 * 2 * nnz[lv]
+            flops["backproject"] += 2 * nnz[lv]
+        else:
+            flops["project"] += 2 * nnz[lv]
+            flops["backproject"] += 2 * 2 * nnz[lv]
+    traced = sum(v[0] for v in trace.values() if v[1])
+    kernels = {}
+    for k, (t, c) in trace.items():
+        if not c:
+            continue
+        e = {"ms_per_step": t / steps, "launches_per_step": c / steps, "share": t / traced}
+        if k in flops:
+            e["tflops_alg"] = flops[k] * steps / (t / 1e3) / 1e12
+            vv = 0
+            for lv in range(L):
+                calls = (2 if k == "project" else 1) if (L == 1 or lv < L - 1) else 1
+                vv += calls * (n >> lv) ** 3 * K
+            e["gups"] = vv * steps / (t / 1e3) / 1e9
+        kernels[k] = e
+    return kernels
+
+
+def time_steps(rec, vol, steps, warmup, barrier=lambda: None, clocks=None):
+    """`warmup` untimed iterations, then `steps` timed ones between CUDA
+    events (launch count and per-family trace taken over the timed ones)."""
+    import torch
+    from paper_2103_10329_gb300 import mgct
+    for _ in range(warmup):
+        rec.iterate(vol)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    mgct.trace_enable(True)
+    mgct.launch_count(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        rec.iterate(vol)
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = mgct.launch_count()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    trace = mgct.trace_read()
+    trace0 = mgct.trace_read(level=0)
+    mgct.trace_enable(False)
+    clk = clocks.stop() if clocks else None
+    return ms, launches, trace, trace0, clk
+
+
 def gpu_arm(args, rank, world):
     import torch
     from paper_2103_10329_gb300 import build, mgct
@@ -662,13 +945,12 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_device(dev)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    W = make_workload(args.workload)
-    g, b, truth = W["geom"], W["b"], W["truth"]
-    n, K, L = W["n"], W["views"], W["levels"]
-    rec = mgct.Reconstructor(g)
-    rec.prepare(b)
-    vol = torch.zeros((n, n, n), device=dev, dtype=torch.float32)
-    units = units_per_step(n, K, L)
+    sm_clock = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12  # TFLOP/s
+    try:
+        mp = mgct.measure_onchip_peaks()
+    except Exception:  # noqa: BLE001
+        mp = None
 
     def barrier():
         if world > 1:
@@ -681,130 +963,35 @@ def gpu_arm(args, rank, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
-    for _ in range(args.warmup):
-        rec.iterate(vol)
-    torch.cuda.synchronize()
-    # ---- device-resident timed region
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    mgct.trace_enable(True)
-    mgct.launch_count(reset=True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(args.steps):
-        rec.iterate(vol)
-    ev1.record()
-    torch.cuda.synchronize()
-    launches = mgct.launch_count()
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    trace = mgct.trace_read()
-    trace0 = mgct.trace_read(level=0)
-    mgct.trace_enable(False)
-    clk = clocks.stop()
+    # ---- the headline workload, inputs resident on the device
+    W = make_workload(args.workload)
+    W["name"] = args.workload
+    g, b, truth = W["geom"], W["b"], W["truth"]
+    n, K, L = W["n"], W["views"], W["levels"]
+    rec = mgct.Reconstructor(g)
+    rec.prepare(b)
+    vol = torch.zeros((n, n, n), device=dev, dtype=torch.float32)
+    units = units_per_step(n, K, L)
+    ms, launches, trace, trace0, clk = time_steps(rec, vol, args.steps, args.warmup, barrier,
+                                                  ClockSampler(dev.index))
     ms_max, total_units = aggregate(ms, units * args.steps, dev)
     value = total_units / (ms_max / 1e3) / 1e9
-
-    # ---- per-kernel work and the dominant kernel's roofline
     nnz = [count_nnz(W["theta"], W["z"], W["pitch"], n >> lv, W["nu"] >> lv, W["nu"] >> lv) for lv in range(L)]
-    flops = {"project": 0.0, "backproject": 0.0}
-    for lv in range(L):
-        if L == 1 or lv < L - 1:
-            flops["project"] += 2 * 2 * nnz[lv]
-            flops["backproject"] += 2 * nnz[lv]
-        else:
-            flops["project"] += 2 * nnz[lv]
-            flops["backproject"] += 2 * 2 * nnz[lv]
-    kern_ms = {k: v[0] for k, v in trace.items() if v[1]}
-    traced = sum(kern_ms.values())
-    dom = max(kern_ms, key=kern_ms.get)
-    sm_clock = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12  # TFLOP/s
-    kernels = {}
-    for k, (t, c) in trace.items():
-        if not c:
-            continue
-        e = {"ms_per_step": t / args.steps, "launches_per_step": c / args.steps, "share": t / traced}
-        if k in flops:
-            e["tflops_alg"] = flops[k] * args.steps / (t / 1e3) / 1e12
-            # voxel-view updates done by this kernel per step: on the Landweber
-            # grids two projections and one back-projection, on the coarsest
-            # grid one of each (OS-EMTR)
-            vv = 0
-            for lv in range(L):
-                calls = (2 if k == "project" else 1) if (L == 1 or lv < L - 1) else 1
-                vv += calls * (n >> lv) ** 3 * K
-            e["gups"] = vv * args.steps / (t / 1e3) / 1e9
-        kernels[k] = e
-    if dom in flops:
-        # the dominant family's grid-0 launches: one launch = one A (or A^T)
-        # over all views of the finest grid
-        t0_ms, t0_n = trace0[dom]
-        avg_ms = t0_ms / max(t0_n, 1)
-        tr = traffic_record("k_" + dom)
-        # the binding floor per launch: max of HBM (one volume + one
-        # sinogram), on-chip gather (4 B per tap against L1 at 128 B/clk/SM)
-        # and FP32 (1 FMA per tap + ~8 flop of weight evaluation per sample)
-        t_s = avg_ms / 1e3
-        hbm_b = 4 * (n ** 3 + K * W["nu"] ** 2)
-        l1_peak = SMS * 128 * sm_clock * 1e6  # B/s
-        gather_b = 4 * nnz[0]
-        fl = 2 * nnz[0] + 8 * (nnz[0] / 4)
-        floors = {"hbm_ms": hbm_b / (peaks.get("hbm_gbs", 6790.0) * 1e9) * 1e3,
-                  "onchip_gather_ms": gather_b / l1_peak * 1e3,
-                  "fp32_ms": fl / (fp32_peak * 1e12) * 1e3}
-        roof = {"kernel": "k_" + dom, "launches": "grid 0 (the finest grid)", "bound": "alu",
-                "binding_floor": "on-chip gather (L1), the largest of the three floors",
-                "achieved": gather_b / t_s / 1e9, "peak": l1_peak / 1e9, "unit": "GB/s",
-                "frac": gather_b / t_s / l1_peak,
-                "def": "frac = t_floor / t_measured, t_floor = max(HBM, on-chip gather, FP32 floors); "
-                       "achieved = 4 B per nonzero of A per launch / launch time, peak = "
-                       f"{SMS} SMs x 128 B/clk x {sm_clock:.0f} MHz of L1",
-                "floors_ms": floors, "avg_launch_ms": avg_ms, "launches_timed": t0_n,
-                "work": f"{nnz[0]:.4g} nonzeros of A per launch (4 bilinear taps per in-volume sample)",
-                "traffic": tr["bytes_per_launch"] if tr else None,
-                "fp32": {"achieved_tflops": fl / t_s / 1e12, "peak_tflops": fp32_peak, "frac": fl / t_s / 1e12 / fp32_peak,
-                         "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_clock:.0f} MHz"},
-                "hbm": {"bytes_alg": hbm_b, "frac_of_measured": hbm_b / t_s / 1e9 / peaks.get("hbm_gbs", 6790.0),
-                        "ncu_bytes_per_launch": tr["bytes_per_launch"] if tr else None}}
-        # the on-chip peaks measured by the library's microbenchmarks, beside
-        # the derived ones the fraction uses
-        try:
-            mp = mgct.measure_onchip_peaks()
-            roof["measured_onchip"] = {
-                "fp32_tflops": mp["fp32_tflops"], "lds_gbs": mp["lds_gbs"],
-                "how": "mgct_measure_onchip_peaks: independent FMA chains; conflict-free 16-byte shared loads",
-                "gather_frac_of_measured_lds": gather_b / t_s / 1e9 / mp["lds_gbs"],
-                "fp32_frac_of_measured": fl / t_s / 1e12 / mp["fp32_tflops"]}
-        except Exception as ex:  # noqa: BLE001
-            roof["measured_onchip"] = {"error": f"{type(ex).__name__}: {ex}"[:200]}
-    else:
-        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": None}
+    kernels = kernel_table(W, nnz, trace, args.steps)
+    roofs = family_rooflines(W, nnz, trace0, peaks, sm_clock, fp32_peak, mp)
+    dom = max(roofs, key=lambda k: roofs[k]["avg_launch_ms"] * roofs[k]["launches_timed"]) if roofs else None
+    roof = roofs[dom] if dom else {"bound": "onchip-gather", "achieved": None, "peak": None, "unit": "GB/s",
+                                   "frac": None, "traffic": None}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step
+    # copies the data b from pinned host memory and the estimate back
     e2e = None
     if not args.no_e2e:
         hb = torch.empty(b.shape, dtype=torch.float32, pin_memory=True)
         hb.copy_(b)
         hv = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
-        bdev = torch.empty_like(b)
         stream = torch.cuda.current_stream()
-        for _ in range(2):
-            bdev.copy_(hb, non_blocking=True)
-            rec.prepare(bdev)
-            rec.iterate(vol)
-            hv.copy_(vol, non_blocking=True)
+        bdev = b  # the device buffer the data land in (overwritten every step)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -819,161 +1006,106 @@ def gpu_arm(args, rank, world):
         barrier()
         ems = max_over_ranks(e0.elapsed_time(e1))
         e2e = {"value": total_units / (ems / 1e3) / 1e9, "unit": "GUPS", "ms_per_step": ems / args.steps,
-               "h2d_bytes_per_step": hb.numel() * 4, "d2h_bytes_per_step": hv.numel() * 4}
-        rec.prepare(b)
+               "h2d_bytes_per_step": hb.numel() * 4, "d2h_bytes_per_step": hv.numel() * 4,
+               "path": "pinned host b -> device, mgct_multigrid_prepare + mgct_multigrid_iteration, "
+                       "estimate -> pinned host, all inside the timed region"}
+        del hb, hv
 
-    # ---- time to accuracy: PMGL vs SIRT at equal fine-grid cost (FP32), and
-    # the 16-bit storage forms against the plain FP32 two-iteration RMSE E2
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    sample_vol = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle as O
+        O.build()
+        sample_vol = truth.double().cpu().numpy()
+        gups, t, cnt, thr, ta, tat = oracle_sample(args.workload, target_s=args.cpu_seconds, vol=sample_vol)
+        cpu = {"value": gups, "unit": "GUPS", "cores": thr, "kind": "oracle",
+               "sample": (f"FP64 oracle A and A^T at grid 0 on {cnt} of {K} views ({t:.1f} s)" if n < 1024 else
+                          f"FP64 oracle at grid 0: A over one of {K} views ({ta:.1f} s, {thr} threads) and its "
+                          f"A^T on {ROW_SAMPLE} of {W['nu']} detector rows scaled to the view ({tat:.1f} s; one "
+                          f"thread: the oracle caps its private FP64 volumes at 8 GB)"),
+               "oracle_seconds": {"A": ta, "AT": tat}}
+    main_name = args.workload
+    del rec, vol, b, truth, sample_vol
+    g.close()
+    W = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    # ---- secondary: the 256^3 / 720-view workload (and its time to accuracy)
+    second = None
     tta = None
-    if not args.no_tta and rank == 0:
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
+    beside = None
+    if not args.no_secondary and main_name != "c2":
+        W = make_workload("c2")
+        W["name"] = "c2"
+        g, b, truth = W["geom"], W["b"], W["truth"]
+        n2, K2, L2 = W["n"], W["views"], W["levels"]
+        rec = mgct.Reconstructor(g)
+        rec.prepare(b)
+        vol = torch.zeros((n2, n2, n2), device=dev, dtype=torch.float32)
+        ms2, _, tr2, tr20, clk2 = time_steps(rec, vol, 5, 3, barrier, ClockSampler(dev.index))
+        u2 = units_per_step(n2, K2, L2)
+        nnz2 = [count_nnz(W["theta"], W["z"], W["pitch"], n2 >> lv, W["nu"] >> lv, W["nu"] >> lv)
+                for lv in range(L2)]
+        second = {"config": workload_config("c2"), "value": u2 * 5 / (ms2 / 1e3) / 1e9, "unit": "GUPS",
+                  "ms_per_step": ms2 / 5, "steps": 5, "warmup": 3, "clocks": clk2,
+                  "kernels": kernel_table(W, nnz2, tr2, 5),
+                  "rooflines": family_rooflines(W, nnz2, tr20, peaks, sm_clock, fp32_peak, mp)}
+    elif main_name == "c2":
+        W = make_workload("c2")
+        W["name"] = "c2"
+        g, b, truth = W["geom"], W["b"], W["truth"]
+        rec = mgct.Reconstructor(g)
+        rec.prepare(b)
+        vol = torch.zeros((W["n"],) * 3, device=dev, dtype=torch.float32)
 
-        def run_iters(storage, iters, net=None, bilateral=None):
-            v = torch.zeros_like(vol)
-            out = []
-            tot = 0.0
-            for _ in range(iters):
+    if W is not None and not args.no_tta and rank == 0:
+        tta = time_to_accuracy(args, W, rec, g, b, truth, vol)
+        rec.prepare(b)
+    if W is not None and not args.no_cpu and not args.no_beside and rank == 0 and world == 1:
+        # a side measurement: its failure is reported, not fatal to the line
+        try:
+            vol_np = truth.double().cpu().numpy()
+            _, _, cnt, _, ta, tat = oracle_sample("c2", target_s=args.cpu_seconds, vol=vol_np)
+            beside = oracle_beside((cnt, ta, tat, vol_np), (g, b), full_c2=args.oracle_full)
+        except Exception as ex:  # noqa: BLE001
+            beside = {"error": f"{type(ex).__name__}: {ex}"[:300]}
+            try:
                 torch.cuda.synchronize()
-                s0.record()
-                if net is None:
-                    rec.iterate(v, storage=storage, bilateral=bilateral)
-                else:
-                    rec.iterate_learned(v, net, storage=storage)
-                s1.record()
-                torch.cuda.synchronize()
-                tot += s0.elapsed_time(s1)
-                out.append((tot, roi_rmse(v, truth)))
-            return out
-
-        base = run_iters(torch.float32, 2)
-        e2 = base[-1][1]
-        vs = torch.zeros_like(vol)
-        ws = mgct.workspace(g, mgct.WS_LANDWEBER, 0)
-        s0.record()
-        for _ in range(2):
-            mgct.landweber_step(g, vs, b, precond=False, ws=ws)
-        s1.record()
-        torch.cuda.synchronize()
-        tta = {"rmse_def": "RMS(mu - truth) / range(truth) over r <= 0.9R, |z| <= 0.9R",
-               "E2_pmgl_fp32_2iter": e2, "pmgl_fp32_2iter_ms": base[-1][0],
-               "sirt_2iter_ms": s0.elapsed_time(s1), "sirt_2iter_rmse_roi": roi_rmse(vs, truth),
-               "forms": {}}
-        # Fig. 2 analogue: OS-EMTR (Eq. 3, M = 8 subsets) at full resolution
-        del vs
-        ones = torch.ones_like(vol)
-        pi = mgct.project(g, ones)
-        del ones
-        we = mgct.workspace(g, mgct.WS_OSEMTR, 0)
-        ve = torch.zeros_like(vol)
-        em, tot = [], 0.0
-        for _ in range(10):
-            torch.cuda.synchronize()
-            s0.record()
-            mgct.osemtr_pass(g, ve, b, pi, n_subsets=8, ws=we)
-            s1.record()
-            torch.cuda.synchronize()
-            tot += s0.elapsed_time(s1)
-            em.append((tot, roi_rmse(ve, truth)))
-        tta["osemtr_full_res"] = {"subsets": 8, "per_pass_ms_cum": [e[0] for e in em],
-                                  "per_pass_rmse_roi": [e[1] for e in em]}
-        del ve, we, pi
-        net = None
-        if not args.no_learned:
-            t0 = time.perf_counter()
-            net, train_info = train_correction(args.learn_phantoms, args.learn_steps)
-            train_info["wall_s"] = time.perf_counter() - t0
-            tta["learned_training"] = train_info
-        forms = [("fp32", torch.float32, False), ("bf16", torch.bfloat16, False), ("fp16", torch.float16, False)]
-        if net is not None:
-            forms += [("learned_fp32", torch.float32, True), ("learned_bf16", torch.bfloat16, True)]
-        # Alg. 1's BilateralFilter (no parameters in the paper): sigma_s = 1 voxel,
-        # sigma_r = 0.2, radius 1, the best of five settings tried on this workload
-        bil = (1.0, 0.2, 1)
-        forms += [("bilateral_fp32", torch.float32, "bil"), ("bilateral_bf16", torch.bfloat16, "bil")]
-        tta["bilateral"] = {"sigma_s_voxels": bil[0], "sigma_r": bil[1], "radius": bil[2],
-                            "chosen": "best of (1, 0.05, 1), (1, 0.1, 1), (1, 0.2, 1), (1.5, 0.1, 2), (0.8, 0.1, 1) "
-                                      "on this workload; E2 stays the plain form's"}
-        # a preconditioner fitted to the measured PSF of A^T A (in place of Eq. 5)
-        from paper_2103_10329_gb300 import psf as PSF
-        t0 = time.perf_counter()
-        kern, _ = PSF.derived_preconditioner(g)
-        torch.cuda.synchronize()
-        fit_s = time.perf_counter() - t0
-        g.set_preconditioner(kern)
-        hist_psf = run_iters(torch.float32, 3)
-        g.set_preconditioner(None)
-        reach = next(((i + 1, t) for i, (t, e) in enumerate(hist_psf) if e <= e2 * (1 + 1e-3)), None)
-        tta["forms"]["psf_kernel_fp32"] = {"per_iter_ms_cum": [h[0] for h in hist_psf],
-                                           "per_iter_rmse_roi": [h[1] for h in hist_psf],
-                                           "iters_to_E2": reach[0] if reach else None,
-                                           "ms_to_E2": reach[1] if reach else None}
-        tta["psf_kernel"] = {"kernel_z0_plane": kern[1].tolist(), "kernel_z1_plane": kern[2].tolist(),
-                             "measure_and_fit_s": fit_s,
-                             "per_iter_ms_cum": [h[0] for h in hist_psf], "per_iter_rmse_roi": [h[1] for h in hist_psf]}
-        for name, st, use_net in forms:
-            if use_net == "bil":
-                hist = run_iters(st, 3, None, bil)
-            else:
-                hist = run_iters(st, 3, net if use_net else None)
-            reach = next(((i + 1, t) for i, (t, e) in enumerate(hist) if e <= e2 * (1 + 1e-3)), None)
-            tta["forms"][name] = {"per_iter_ms_cum": [h[0] for h in hist], "per_iter_rmse_roi": [h[1] for h in hist],
-                                  "iters_to_E2": reach[0] if reach else None,
-                                  "ms_to_E2": reach[1] if reach else None}
-        tta["E2_tolerance"] = "RMSE <= E2 (1 + 1e-3)"
-        if not args.no_literal:
-            tta["literal_rmse_1e-3"] = {
-                args.workload: literal_tta(rec, g, truth, net),
-                "c1": literal_tta(None, None, None, net, workload="c1"),
-            }
-            rec.prepare(b)
+                torch.cuda.empty_cache()
+            except Exception:  # noqa: BLE001
+                pass
+    if W is not None:
+        g.close()
 
     hbm = None
     if not args.no_hbm and rank == 0:
         hbm = hbm_kernel_rates(peaks.get("hbm_gbs", 6790.0))
 
-    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
-    cpu = beside = None
-    if not args.no_cpu and rank == 0 and world == 1:
-        import oracle as O
-        O.build()
-        vol_np = truth.double().cpu().numpy()
-        gups, t, cnt, thr, ta, tat = oracle_sample(args.workload, target_s=args.cpu_seconds, vol=vol_np)
-        cpu = {"value": gups, "unit": "GUPS", "cores": thr, "kind": "oracle",
-               "sample": f"FP64 oracle A and A^T at grid 0 on {cnt} of {K} views ({t:.1f} s)"}
-        if not args.no_beside and args.workload == "c2":
-            # a side measurement: its failure (say, too little free device
-            # memory for the 1024^3 calls) is reported, not fatal to the line
-            try:
-                beside = oracle_beside((cnt, ta, tat, vol_np), (g, b), full_c2=args.oracle_full)
-            except Exception as ex:  # noqa: BLE001
-                import torch
-                beside = {"error": f"{type(ex).__name__}: {ex}"[:300]}
-                try:
-                    torch.cuda.synchronize()
-                    torch.cuda.empty_cache()
-                except Exception:  # noqa: BLE001
-                    pass
-
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(workload_config(args.workload), parallelism=f"replicas x{world}"),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "kernels": kernels, "hbm_kernels": hbm, "time_to_accuracy": tta,
-                "oracle_beside": beside}
+                "config": dict(workload_config(main_name), parallelism=f"replicas x{world}"),
+                "roofline": roof, "rooflines": roofs, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk, "kernels": kernels,
+                "measured_onchip": mp and {"fp32_tflops": mp["fp32_tflops"], "lds_gbs": mp["lds_gbs"],
+                                           "how": "mgct_measure_onchip_peaks: independent FMA chains; "
+                                                  "conflict-free 16-byte shared loads"},
+                "secondary": second, "hbm_kernels": hbm, "time_to_accuracy": tta, "oracle_beside": beside}
         print(json.dumps(line), flush=True)
-    g.close()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mgct", choices=["mgct", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 256^3 / 720-view secondary line (and its time to accuracy)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tta", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

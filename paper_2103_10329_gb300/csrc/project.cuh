@@ -447,8 +447,10 @@ __device__ __forceinline__ float zquad_sample(const typename VolTraits<VT>::elem
     return fmaf(tz, a.y - a.x, a.x);
 }
 
+template <typename E>
 struct ColTab {
-    float tb, tb2, roff, pad;  // fraction along b (twice), row offset (int bits)
+    float tb, tb2;  // fraction along b (twice: a float pair)
+    const E *row;   // entries of the sample's (plane, b) row
 };
 
 // Layouts of the column projector's z-fastest copies (entry (i, jb + QD_PAD,
@@ -476,7 +478,7 @@ template <typename VT, int LAYOUT>
 __device__ __forceinline__ RaySum column_rays(const ProjArgs &a, const float4 *__restrict__ ct, int jv, bool row_ok,
                                               const typename ZElem<VT, LAYOUT>::type *__restrict__ zqy,
                                               const typename ZElem<VT, LAYOUT>::type *__restrict__ zqx,
-                                              ColTab *__restrict__ tab) {
+                                              ColTab<typename ZElem<VT, LAYOUT>::type> *__restrict__ tab) {
     using E = typename ZElem<VT, LAYOUT>::type;
     // {ax, rb, rb_lo, pb}, {pb_lo, ez0, ez0_lo, ezc}, {ezc_lo, e10, e10_lo, e1c}, {e1c_lo, 0, 0, 0}
     const float4 t0 = __ldg(ct), t1 = __ldg(ct + 1), t2 = __ldg(ct + 2), t3 = __ldg(ct + 3);
@@ -516,17 +518,17 @@ __device__ __forceinline__ RaySum column_rays(const ProjArgs &a, const float4 *_
         // lane l: plane c0 + l of this warp's table
         const int pc = c0 + lane;
         float tbv = 0.0f;
-        int roff = (int)emax * side;  // plane 0, corner b = n + 1 (or n): zero entries
+        const E *row = base + (size_t)emax * side;  // plane 0, corner b = n + 1 (or n): zero entries
         if (pc <= I1) {
             int Ib;
             float phib;
             split_coord(df_add(df_add(pb, df_mul_f(rb, __fsub_rn((float)pc, ic))), DF{ic, 0.0f}), Ib, phib);
             const unsigned bq = min((unsigned)(Ib + QD_PAD), emax);
-            roff = (pc * side + (int)bq) * side;
+            row = base + ((size_t)pc * side + bq) * side;
             tbv = phib;
         }
         __syncwarp();
-        tab[lane] = ColTab{tbv, tbv, __int_as_float(roff), 0.0f};
+        tab[lane] = ColTab<E>{tbv, tbv, row};
         __syncwarp();
         const int cnt = min(PC_TAB, I1 - c0 + 1);
         float part = 0.0f;
@@ -537,13 +539,13 @@ __device__ __forceinline__ RaySum column_rays(const ProjArgs &a, const float4 *_
             float tz[PC_BATCH];
 #pragma unroll
             for (int j = 0; j < PC_BATCH; ++j) {
-                const float4 te = reinterpret_cast<const float4 *>(tab)[kk + j];
-                tb[j] = make_float2(te.x, te.y);
+                const ColTab<E> te = tab[kk + j];
+                tb[j] = make_float2(te.tb, te.tb2);
                 const unsigned zlo = (unsigned)zpos;
                 const int zhi = (int)(zpos >> 32);
                 tz[j] = __uint_as_float(0x3f800000u | (zlo >> 9)) - 1.0f;
                 const unsigned zq = min((unsigned)(zhi + QD_PAD), emax);
-                const E *q = base + (unsigned)(__float_as_int(te.z) + (int)zq);
+                const E *q = te.row + zq;
                 Q[j][0] = __ldg(q);
                 if constexpr (NL == 2) Q[j][1] = __ldg(q + 1);
                 zpos += zstep;
@@ -573,7 +575,7 @@ template <typename VT, int LAYOUT, typename Epi>
 __global__ void __launch_bounds__(PC_COLS *PC_ROWS, MGCT_PC_MINB)
     k_project_col(ProjArgs a, const float4 *__restrict__ cols, const typename ZElem<VT, LAYOUT>::type *__restrict__ zqy,
                   const typename ZElem<VT, LAYOUT>::type *__restrict__ zqx, Epi epi) {
-    __shared__ __align__(16) ColTab tab[PC_COLS][PC_TAB];
+    __shared__ __align__(16) ColTab<typename ZElem<VT, LAYOUT>::type> tab[PC_COLS][PC_TAB];
     const int rtiles = (a.nv + PC_ROWS - 1) / PC_ROWS;
     const int group = blockIdx.z / rtiles, rt = blockIdx.z - group * rtiles;
     const int i = group * PC_VG + blockIdx.y;  // batch index
@@ -614,11 +616,9 @@ int launch_project_col(const mgct_geom *g, int level, int view0, int nviews, int
 }
 
 // The column projector applies where the geometry has no detector tilt (its
-// column table exists at every grid) and its entry offsets fit 31 bits
-// (volumes up to about 1290^3).
+// column table exists at every grid).
 inline bool use_column_projector(const mgct_geom *g, int level) {
-    const size_t n = g->lev[level].n, side = quad_side(g->lev[level].n);
-    return g->separable && g->lev[level].d_cols_df != nullptr && n * side * side < ((size_t)1 << 31);
+    return g->separable && g->lev[level].d_cols_df != nullptr;
 }
 
 template <typename VT, typename Epi>

@@ -15,7 +15,8 @@ Alternation, coarse grids first:
     Levenberg-Marquardt damping and a trust region (one pixel of the grid)
     keep the steps safe where the data pin a parameter weakly (a source and
     a detector shift along the same axis move the projections alike, up to
-    the magnification across the volume's depth).
+    the magnification across the object's depth); a random-walk prior across
+    consecutive views (the drift model) pins that combination.
 
 Every operator is one of the library's: the projector, the geometry gradient,
 restriction and the multigrid iteration.  The host solves the 5 x 5 systems.
@@ -34,10 +35,45 @@ def _restrict_to(x: torch.Tensor, level: int, fn) -> torch.Tensor:
     return x
 
 
+def _block_tridiag_solve(D, O, rhs):
+    """Solve the block-tridiagonal system with diagonal blocks D[k] (5 x 5),
+    off-diagonal blocks O (the same symmetric 5 x 5 above and below) and
+    right-hand side rhs[k] (block Thomas algorithm, k in acquisition order)."""
+    K = D.shape[0]
+    Dp = np.empty_like(D)
+    rp = np.empty_like(rhs)
+    Dp[0], rp[0] = D[0], rhs[0]
+    for k in range(1, K):
+        m = O @ np.linalg.inv(Dp[k - 1])
+        Dp[k] = D[k] - m @ O
+        rp[k] = rhs[k] - m @ rp[k - 1]
+    x = np.empty_like(rhs)
+    x[-1] = np.linalg.solve(Dp[-1], rp[-1])
+    for k in range(K - 2, -1, -1):
+        x[k] = np.linalg.solve(Dp[k], rp[k] - O @ x[k + 1])
+    return x
+
+
 def newton_drift_step(geom, mu_l: torch.Tensor, b_l: torch.Tensor, phi: np.ndarray, level: int,
-                      half_diag_px: float, damping: float = 1e-2) -> tuple[np.ndarray, float]:
+                      half_diag_px: float, damping: float = 1e-2, smooth: float = 0.3,
+                      trust: float = 1.0) -> tuple[np.ndarray, float]:
     """One damped Newton step on every view's drift at grid `level`; returns
-    (new phi, loss before the step)."""
+    (new phi, loss before the step).
+
+    The loss is 1/2 |A(phi) mu - b|^2 plus a random-walk prior, (w_j / 2)
+    sum_k (phi_kj - phi_k-1,j)^2 over consecutive views, whose weight w_j is
+    `smooth` times the median curvature of parameter type j.  A view's data
+    pin a source and a detector shift along the same axis only through the
+    magnification across the object's depth, which changes with the view's
+    angle; the prior ties each view to its neighbours in acquisition order,
+    whose angles differ, and so pins the combination one view alone does
+    not.  The Newton system is block tridiagonal (5 x 5 blocks).  Of 0.1,
+    0.3 and 1.0 tried at 64^3 / 90 views, 0.3 recovered the projection shift
+    along u (ds_u + dd_u) best, 1.0 the single parameters.  Two directions
+    stay free whatever the prior: a source and a detector shift that cancel
+    at the volume centre (pinned only through the depth), and a vertical
+    offset common to all views, which equals a vertical shift of the
+    object."""
     K = phi.shape[0]
     eps = np.array([0.05, 0.05, 0.05, 0.05, 0.05 / max(half_diag_px, 1.0)])
 
@@ -57,14 +93,23 @@ def newton_drift_step(geom, mu_l: torch.Tensor, b_l: torch.Tensor, phi: np.ndarr
         gj, _ = grad_at(p)
         H[:, :, j] = (gj - g0) / eps[j]
     H = 0.5 * (H + np.transpose(H, (0, 2, 1)))
-    diag = np.abs(np.diagonal(H, axis1=1, axis2=2)) + 1e-30
-    A = H + damping * diag[:, :, None] * np.eye(5)[None]
-    try:
-        step = -np.linalg.solve(A, g0[:, :, None])[:, :, 0]
-    except np.linalg.LinAlgError:
-        step = -g0 / diag
-    # trust region: one pixel of this grid (and the matching tilt)
-    lim = np.array([1.0, 1.0, 1.0, 1.0, 1.0 / max(half_diag_px, 1.0)]) * (1 << level)
+    hd = np.abs(np.diagonal(H, axis1=1, axis2=2))
+    w = smooth * np.median(hd, axis=0) + 1e-30
+    # gradient and Hessian of the prior
+    d = np.diff(phi, axis=0) * w
+    gp = np.zeros_like(phi)
+    gp[1:] += d
+    gp[:-1] -= d
+    cnt = np.full(K, 2.0)
+    cnt[0] = cnt[-1] = 1.0 if K > 1 else 0.0
+    D = H + damping * (hd + 1e-30)[:, :, None] * np.eye(5)[None] + (cnt[:, None] * w[None, :])[:, :, None] * np.eye(5)[None]
+    O = -np.diag(w)
+    if K > 1:
+        step = _block_tridiag_solve(D, O, -(g0 + gp))
+    else:
+        step = -np.linalg.solve(D[0], g0[0] + gp[0])[None]
+    # trust region: `trust` pixels of this grid (and the matching tilt)
+    lim = trust * np.array([1.0, 1.0, 1.0, 1.0, 1.0 / max(half_diag_px, 1.0)]) * (1 << level)
     step = np.clip(step, -lim, lim)
     geom.set_drift(phi)
     return phi + step, loss
@@ -72,11 +117,12 @@ def newton_drift_step(geom, mu_l: torch.Tensor, b_l: torch.Tensor, phi: np.ndarr
 
 def estimate(geom, b: torch.Tensor, half_diag_px: float, schedule=((1, 2), (0, 2)), mg_iters: int = 2,
              newton_steps: int = 2, phi0: np.ndarray | None = None, truth_phi: np.ndarray | None = None,
-             mu: torch.Tensor | None = None):
+             mu: torch.Tensor | None = None, **step_kw):
     """Alternate image and drift steps.  `schedule` lists (grid, rounds);
     each round runs `mg_iters` multigrid iterations, then `newton_steps`
-    drift steps on that grid.  Returns (mu, phi, history); with `truth_phi`
-    the history records the drift RMSE per parameter type after each round."""
+    drift steps on that grid (keyword arguments `step_kw` go to
+    newton_drift_step).  Returns (mu, phi, history); with `truth_phi` the
+    history records the drift RMSE per parameter type after each round."""
     K = geom.n_views
     phi = np.zeros((K, 5)) if phi0 is None else np.array(phi0, dtype=np.float64)
     n = geom.n
@@ -94,7 +140,7 @@ def estimate(geom, b: torch.Tensor, half_diag_px: float, schedule=((1, 2), (0, 2
             mu_l = _restrict_to(mu, level, mgct.restrict_volume).contiguous()
             loss = None
             for _ in range(newton_steps):
-                phi, loss = newton_drift_step(geom, mu_l, b_l, phi, level, half_diag_px)
+                phi, loss = newton_drift_step(geom, mu_l, b_l, phi, level, half_diag_px, **step_kw)
             rec_h = {"level": level, "loss_before_last_step": loss}
             if truth_phi is not None:
                 rec_h["drift_rmse"] = np.sqrt(np.mean((phi - truth_phi) ** 2, axis=0)).tolist()

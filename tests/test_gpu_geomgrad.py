@@ -173,11 +173,15 @@ def test_geometry_grad_full_size_sampled():
 def test_joint_estimation_recovers_per_view_drift():
     """Every view drifts (source and detector offsets along both detector
     axes and the detector tilt, Gaussian random walks of 0.3 px per view, as
-    in the drift workload); starting from no drift, the alternation of
-    multigrid iterations with per-view Newton steps built on the geometry
-    gradient recovers the drift: its RMSE falls well below the drift itself
-    for the parameters the data pin (the detector offsets and the tilt), and
-    the image comes out closer to the phantom than without the correction."""
+    in the drift workload).  Starting from no drift, the alternation of
+    multigrid iterations with Newton steps built on the geometry gradient
+    recovers what the data determine: the tilt and the projection shift along
+    u of the volume centre (ds_u + dd_u at magnification 2) to a small
+    fraction of the drift, every parameter type better than no correction,
+    and an image much closer to the phantom than without the correction.
+    (A source and a detector shift cancelling at the centre, and a vertical
+    offset common to all views, which equals moving the object, are pinned
+    only weakly or not at all.)"""
     from paper_2103_10329_gb300 import joint, mgct
     K, n, nu = 90, 64, 96
     half = 0.5 * np.sqrt(2.0) * nu
@@ -189,14 +193,14 @@ def test_joint_estimation_recovers_per_view_drift():
     gt.close()
     g = gpu_geom(scan_desc(n, nu, nu, K, 2104, levels=2))
     mu, phi, hist = joint.estimate(g, b, half, schedule=((1, 3), (0, 3)), truth_phi=true)
+    err = phi - true
     rms0 = np.sqrt(np.mean(true ** 2, axis=0))
-    rms1 = np.sqrt(np.mean((phi - true) ** 2, axis=0))
-    # detector offsets (u, v) and tilt: recovered to a small fraction
-    for j in (2, 3, 4):
-        assert rms1[j] < 0.25 * rms0[j], (j, rms0.tolist(), rms1.tolist(), hist)
-    # every parameter type at least improves on no correction
+    rms1 = np.sqrt(np.mean(err ** 2, axis=0))
+    shift0 = np.sqrt(np.mean((true[:, 0] + true[:, 2]) ** 2))
+    shift1 = np.sqrt(np.mean((err[:, 0] + err[:, 2]) ** 2))
+    assert rms1[4] < 0.25 * rms0[4], (rms0.tolist(), rms1.tolist(), hist)
+    assert shift1 < 0.25 * shift0, (shift0, shift1, hist)
     assert np.all(rms1 < rms0), (rms0.tolist(), rms1.tolist())
-    # the image: closer to the phantom than the uncorrected reconstruction
     g.set_drift(None)
     rec = mgct.Reconstructor(g)
     rec.prepare(b)
@@ -206,6 +210,6 @@ def test_joint_estimation_recovers_per_view_drift():
     t = cuda(truth)
     e_est = float(torch.sqrt(torch.mean((mu - t) ** 2)))
     e_none = float(torch.sqrt(torch.mean((mu0 - t) ** 2)))
-    assert e_est < 0.7 * e_none, (e_est, e_none)
-    print(f"\njoint estimation: drift rms {rms0.round(3).tolist()} -> {rms1.round(3).tolist()}; "
-          f"image rmse {e_none:.4g} -> {e_est:.4g}")
+    assert e_est < 0.5 * e_none, (e_est, e_none)
+    print(f"\njoint estimation: drift rms {rms0.round(3).tolist()} -> {rms1.round(3).tolist()}; u shift "
+          f"{shift0:.3f} -> {shift1:.3f} px; image rmse {e_none:.4g} -> {e_est:.4g}")

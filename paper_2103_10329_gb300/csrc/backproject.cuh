@@ -284,6 +284,8 @@ __global__ void __launch_bounds__(BP_BX *BP_BY *BP_BZ)
 // no atomics, and the order of additions is fixed).  Lanes are adjacent x
 // columns, so the pixel reads of a warp fall on one detector row.
 constexpr int BS_TX = 32, BS_TY = 4, BS_THREADS = BS_TX * BS_TY;
+constexpr float BS_MAGIC = 12582912.0f;  // 1.5 * 2^23
+constexpr int BS_MAGIC_BITS = 0x4B400000;
 
 #ifndef MGCT_BS_PAIRS
 #define MGCT_BS_PAIRS 1
@@ -388,12 +390,17 @@ __global__ void __launch_bounds__(BS_THREADS)
                     // two rows at a time: their crossings floor(fz) are equal or
                     // one apart (0 < E1 < 1), so the pair touches three slab
                     // rows r, r + 1, r + 2 -- three read-modify-writes, not four
+                    // floor(fz) from one addition rounded toward minus infinity
+                    // (fz + 1.5 * 2^23 holds it in its low mantissa bits); a
+                    // row index outside the slab wraps, as unsigned, to the top
+                    // guard rows
+                    const int rbase = BS_MAGIC_BITS + zb - 2;
                     for (; jv + 1 <= vhi; jv += 2, vf += 2.0f, px += 2 * (size_t)a.nu) {
                         const float fz0 = fmaf(vf, E1, E0), fz1 = fmaf(vf + 1.0f, E1, E0);
-                        const float fl0 = floorf(fz0), fl1 = floorf(fz1);
-                        const float t0 = fz0 - fl0, t1 = fz1 - fl1;
-                        const int r = min(max((int)fl0 - zb + 2, 0), ROWS - 3);
-                        const bool same = fl1 == fl0;
+                        const float m0 = __fadd_rd(fz0, BS_MAGIC), m1 = __fadd_rd(fz1, BS_MAGIC);
+                        const float t0 = fz0 - (m0 - BS_MAGIC), t1 = fz1 - (m1 - BS_MAGIC);
+                        const int r = (int)min((unsigned)(__float_as_int(m0) - rbase), (unsigned)(ROWS - 3));
+                        const bool same = __float_as_int(m1) == __float_as_int(m0);
                         const float y0 = hb * to_f32(__ldg(px)), y1 = hb * to_f32(__ldg(px + a.nu));
                         const float a0 = y0 * t0, b0 = y1 * t1;
                         const float lo1 = y1 - b0;

@@ -235,16 +235,23 @@ def make_workload(name, device="cuda"):
                 levels=L)
 
 
-def train_correction(phantoms: int, steps: int):
+def train_correction(phantoms: int, steps: int, kernel=None):
     """The learned correction, trained on the GPU by the library's own kernels
     on pairs the method generates on random 128^3 phantoms (192^2 detector,
-    360 views, 2 grids, 20 ellipsoids each)."""
+    360 views, 2 grids, 20 ellipsoids each).  With `kernel` (a 3x3x3
+    preconditioner in place of Eq. 5, set on every training geometry) the
+    network learns to correct that kernel's step instead."""
     import torch
     from paper_2103_10329_gb300 import learned as LN
     from paper_2103_10329_gb300 import mgct
     t0 = time.perf_counter()
     cases = [LN.make_case(128, 192, 360, 2, seed=20000 + i, count=20) for i in range(phantoms)]
+    if kernel is not None:
+        for geom, _, _ in cases:
+            geom.set_preconditioner(kernel)
     pairs = LN.generate_pairs(cases, iters=2)
+    for geom, _, _ in cases:
+        geom.close()
     del cases
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -628,7 +635,9 @@ def literal_tta(rec, g, truth, net, workload=None, target=1e-3, cap=50):
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     forms = [("fp32", torch.float32, None, False), ("bf16", torch.bfloat16, None, False),
-             ("fp32_fas", torch.float32, None, True), ("bf16_fas", torch.bfloat16, None, True)]
+             ("fp32_fas", torch.float32, None, True), ("bf16_fas", torch.bfloat16, None, True),
+             ("bf16_fas_fp32_every_4th", "refresh4", None, True),
+             ("bf16_fas_fp32_every_2nd", "refresh2", None, True), ("fp16_fas", torch.float16, None, True)]
     if net is not None:
         forms += [("learned_bf16", torch.bfloat16, net, False), ("learned_bf16_fas", torch.bfloat16, net, True)]
     out = {"data": "inverse crime: b = A truth (this library's A on the reconstruction grid), no noise",
@@ -641,7 +650,12 @@ def literal_tta(rec, g, truth, net, workload=None, target=1e-3, cap=50):
         for it in range(1, cap + 1):
             torch.cuda.synchronize()
             s0.record()
-            if nn is None:
+            if isinstance(st, str):
+                # BF16 copies of mu round at about 1e-3 of its range, the
+                # target itself; one float32 iteration in every k lowers the floor
+                k = int(st[len("refresh"):])
+                rec.iterate(v, storage=torch.float32 if it % k == 0 else torch.bfloat16, fas=fas)
+            elif nn is None:
                 rec.iterate(v, storage=st, fas=fas)
             else:
                 rec.iterate_learned(v, nn, storage=st, fas=fas)
@@ -717,14 +731,17 @@ def time_to_accuracy(args, W, rec, g, b, truth, vol):
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
 
-    def run_iters(storage, iters, net=None, bilateral=None):
+    def run_iters(storage, iters, net=None, bilateral=None, learned_iters=None):
+        """Per-iteration (cumulative ms, RMSE_ROI); with `net`, the learned
+        step on the first `learned_iters` iterations (all when None), the
+        plain one after (the gate)."""
         v = torch.zeros_like(vol)
         out = []
         tot = 0.0
-        for _ in range(iters):
+        for it in range(iters):
             torch.cuda.synchronize()
             s0.record()
-            if net is None:
+            if net is None or (learned_iters is not None and it >= learned_iters):
                 rec.iterate(v, storage=storage, bilateral=bilateral)
             else:
                 rec.iterate_learned(v, net, storage=storage)
@@ -808,6 +825,38 @@ def time_to_accuracy(args, W, rec, g, b, truth, vol):
         tta["forms"][name] = {"per_iter_ms_cum": [h[0] for h in hist], "per_iter_rmse_roi": [h[1] for h in hist],
                               "iters_to_E2": reach[0] if reach else None,
                               "ms_to_E2": reach[1] if reach else None}
+    if net is not None:
+        # the gate: the correction on the first iteration only (it gains early
+        # and hurts late), plain Alg. 1 after
+        hist = run_iters(torch.bfloat16, 3, net, learned_iters=1)
+        reach = next(((i + 1, t) for i, (t, e) in enumerate(hist) if e <= e2 * (1 + 1e-3)), None)
+        tta["forms"]["learned_bf16_first_iteration_only"] = {
+            "per_iter_ms_cum": [h[0] for h in hist], "per_iter_rmse_roi": [h[1] for h in hist],
+            "iters_to_E2": reach[0] if reach else None, "ms_to_E2": reach[1] if reach else None}
+    if not args.no_learned:
+        # the correction trained on top of the PSF-derived kernel, against that
+        # kernel's own two-iteration RMSE E_psf2 (which one plain iteration of
+        # it does not reach)
+        t0 = time.perf_counter()
+        net_psf, info_psf = train_correction(args.learn_phantoms, args.learn_steps, kernel=kern)
+        info_psf["wall_s"] = time.perf_counter() - t0
+        tta["learned_psf_training"] = info_psf
+        e_psf2 = hist_psf[1][1]
+        g.set_preconditioner(kern)
+        tta["E_psf2"] = e_psf2
+        for name, st, nn_, li in (("psf_kernel_fp32", torch.float32, None, None),
+                                  ("learned_psf_fp32", torch.float32, net_psf, None),
+                                  ("learned_psf_bf16", torch.bfloat16, net_psf, None),
+                                  ("learned_psf_bf16_first_iteration_only", torch.bfloat16, net_psf, 1)):
+            hist = run_iters(st, 3, nn_, learned_iters=li)
+            r2 = next(((i + 1, t) for i, (t, e) in enumerate(hist) if e <= e2 * (1 + 1e-3)), None)
+            rp = next(((i + 1, t) for i, (t, e) in enumerate(hist) if e <= e_psf2 * (1 + 1e-3)), None)
+            tta.setdefault("psf_forms", {})[name] = {
+                "per_iter_ms_cum": [h[0] for h in hist], "per_iter_rmse_roi": [h[1] for h in hist],
+                "ms_to_E2": r2[1] if r2 else None, "ms_to_E_psf2": rp[1] if rp else None,
+                "iters_to_E_psf2": rp[0] if rp else None}
+        g.set_preconditioner(None)
+        net_psf.close()
     tta["E2_tolerance"] = "RMSE <= E2 (1 + 1e-3)"
     if not args.no_literal:
         tta["literal_rmse_1e-3"] = {

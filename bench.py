@@ -960,6 +960,57 @@ def joint_estimation_c4(seed=SEED + 4, schedule=((2, 2), (1, 2), (0, 2)), mg_ite
             "image_rmse_roi": out_img, "history": hist}
 
 
+def evaluation_1024(args):
+    """The learned correction at the 1024^3 / 1536^2 / 2880-view evaluation
+    size (the headline workload): two multigrid iterations from zero of the
+    plain form (Eq. 5), the PSF-derived kernel, and the correction trained on
+    top of that kernel (128^3 training phantoms, BF16 tensor-core network
+    applied in z-slabs), each with its RMSE (ROI) per iteration and its
+    seconds.  The kernel is fitted on the 256^3 / 720-view geometry of the
+    same family (same distances and detector-to-voxel ratio): the fit's PSF
+    measurement at 1024^3 would take several full A^T A applications."""
+    import torch
+    from paper_2103_10329_gb300 import mgct
+    from paper_2103_10329_gb300 import psf as PSF
+    w2 = WORKLOADS["c2"]
+    from paper_2103_10329_gb300 import synth
+    th2, z2 = synth.trajectory(w2["views"], SEED + 1)
+    g2 = mgct.Geometry(w2["n"], w2["nu"], w2["nu"], th2, z2, synth.default_pitch(w2["nu"]), levels=w2["levels"])
+    kern, _ = PSF.derived_preconditioner(g2)
+    g2.close()
+    t0 = time.perf_counter()
+    net_psf, info = train_correction(args.learn_phantoms, args.learn_steps, kernel=kern)
+    info["wall_s"] = time.perf_counter() - t0
+    W = make_workload("c5")
+    g, b, truth = W["geom"], W["b"], W["truth"]
+    rec = mgct.Reconstructor(g)
+    rec.prepare(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": workload_config("c5")["workload"], "training": info, "forms": {}}
+    for name, k, nn in (("plain_eq5", None, None), ("psf_kernel", kern, None), ("learned_on_psf_bf16", kern, net_psf)):
+        g.set_preconditioner(k)
+        v = torch.zeros_like(truth)
+        hist = []
+        tot = 0.0
+        for _ in range(2):
+            torch.cuda.synchronize()
+            e0.record()
+            if nn is None:
+                rec.iterate(v)
+            else:
+                rec.iterate_learned(v, nn, storage=torch.bfloat16)
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+            hist.append((tot / 1e3, roi_rmse(v, truth)))
+        out["forms"][name] = {"seconds_cum": [h[0] for h in hist], "rmse_roi": [h[1] for h in hist]}
+        del v
+    g.set_preconditioner(None)
+    net_psf.close()
+    g.close()
+    return out
+
+
 def family_rooflines(W, nnz, trace0, peaks, sm_clock, fp32_peak, mp=None):
     """Roofline objects of the projector and back-projector families on the
     finest grid: one grid-0 launch is one A (or A^T) over every view.  The
@@ -1267,6 +1318,8 @@ def main():
                     help="time the oracle's whole two-iteration solve at 256^3 (minutes of CPU)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-joint", action="store_true", help="skip the joint drift estimation (256^3, 720 views)")
+    ap.add_argument("--eval-1024", action="store_true",
+                    help="only the learned correction's evaluation at 1024^3 (plain, PSF kernel, learned)")
     ap.add_argument("--no-hbm", action="store_true", help="skip the HBM-bound kernel rates at 512^3")
     ap.add_argument("--no-literal", action="store_true",
                     help="skip the seconds-to-RMSE<=1e-3 runs on inverse-crime data")
@@ -1278,6 +1331,11 @@ def main():
         if world > 1 and rank != 0:
             return
         reference_arm(args, rank)
+        return
+    if args.eval_1024:
+        from paper_2103_10329_gb300 import build
+        build.build()
+        print(json.dumps({"evaluation_1024": evaluation_1024(args)}), flush=True)
         return
     if world > 1:
         import torch

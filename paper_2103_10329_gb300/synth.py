@@ -201,13 +201,20 @@ def porous_texture(n: int, seed: int, device="cpu", solid: float = 0.3,
     return vol.to(dtype)
 
 
-def poisson_log_data(b: torch.Tensor, photons: float, seed: int) -> torch.Tensor:
+def poisson_log_data(b: torch.Tensor, photons: float, seed: int, chunk: int = 1 << 30) -> torch.Tensor:
     """Photon-counting noise on log data (Eq. 1): I ~ Poisson(I0 exp(-b)),
-    returned as -ln(max(I, 1) / I0).  Works on any device; float32 result."""
+    returned as -ln(max(I, 1) / I0).  Works on any device; float32 result.
+    Sinograms of more than `chunk` elements are drawn a block of whole views
+    at a time (torch's Poisson sampler on the GPU gives wrong counts on
+    tensors of more than 2^31 elements); smaller ones in one draw."""
     g = torch.Generator(device=b.device).manual_seed(seed)
-    lam = photons * torch.exp(-b.to(torch.float32))
-    counts = torch.poisson(lam, generator=g)
-    return -torch.log(torch.clamp(counts, min=1.0) / photons)
+    out = torch.empty(b.shape, dtype=torch.float32, device=b.device)
+    per = max(1, chunk // max(1, b[0].numel())) if b.numel() > chunk else b.shape[0]
+    for k0 in range(0, b.shape[0], per):
+        lam = photons * torch.exp(-b[k0:k0 + per].to(torch.float32))
+        counts = torch.poisson(lam, generator=g)
+        out[k0:k0 + per] = -torch.log(torch.clamp(counts, min=1.0) / photons)
+    return out
 
 
 def random_indices(count: int, limits, seed: int) -> np.ndarray:

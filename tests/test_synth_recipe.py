@@ -80,3 +80,19 @@ def test_poisson_log_data_is_unbiased_at_high_counts():
     assert abs(float(y.mean()) - (1.0 + bias)) < 3e-4
     # and standard deviation 1 / sqrt(I0 e^-b)
     assert abs(float(y.std()) - 1.0 / math.sqrt(1e4 * math.exp(-1.0))) < 5e-4
+
+
+def test_poisson_log_data_in_view_blocks():
+    """Sinograms larger than the block limit are drawn a block of whole views
+    at a time: the same statistics, every view filled, and the single-draw
+    result unchanged below the limit."""
+    b = torch.full((50, 40, 100), 1.0, dtype=torch.float64)
+    y = synth.poisson_log_data(b, 1e4, 5, chunk=7 * 4000 + 13).double()
+    assert y.shape == b.shape and bool(torch.isfinite(y).all())
+    bias = 1.0 / (2 * 1e4 * math.exp(-1.0))
+    assert abs(float(y.mean()) - (1.0 + bias)) < 3e-4
+    assert abs(float(y.std()) - 1.0 / math.sqrt(1e4 * math.exp(-1.0))) < 5e-4
+    per_view = y.reshape(50, -1).std(dim=1)
+    assert float(per_view.min()) > 0.5 * float(per_view.max())
+    small = torch.full((3, 4, 5), 0.5, dtype=torch.float64)
+    assert torch.equal(synth.poisson_log_data(small, 1e4, 9), synth.poisson_log_data(small, 1e4, 9, chunk=60))

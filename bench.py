@@ -1031,7 +1031,7 @@ def family_rooflines(W, nnz, trace0, peaks, sm_clock, fp32_peak, mp=None):
     floors = {"hbm_ms": hbm_b / (peaks.get("hbm_gbs", 6790.0) * 1e9) * 1e3,
               "onchip_gather_ms": gather_b / l1_peak * 1e3,
               "fp32_ms": fl / (fp32_peak * 1e12) * 1e3}
-    names = {"project": "k_project_col", "backproject": "k_backproject_slab"}
+    names = {"project": "k_project_col", "backproject": "k_backproject_reg"}
     out = {}
     for fam, kname in names.items():
         if fam not in trace0 or not trace0[fam][1]:

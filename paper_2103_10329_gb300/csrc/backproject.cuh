@@ -290,6 +290,9 @@ constexpr int BS_MAGIC_BITS = 0x4B400000;
 #ifndef MGCT_BS_PAIRS
 #define MGCT_BS_PAIRS 1
 #endif
+#ifndef MGCT_BS_REG
+#define MGCT_BS_REG 1
+#endif
 template <int NCH>
 struct SlabCfg {
     // voxels per slab: 16 keeps the shared slab at 10 KB so that 16 blocks
@@ -448,6 +451,171 @@ __global__ void __launch_bounds__(BS_THREADS)
     }
 }
 
+// Register form of the solver's A^T (separable geometry, weighted rows, one
+// channel) for grids whose detector rows are finer than the voxels along z:
+// 1/3 < E1 < 1 for every view, column and plane (LevelInfo::e1_lo / e1_hi).
+// As in the slab kernel a thread owns one (x, y) voxel column and ZS voxels
+// z0 .. z0 + ZS - 1 of it, but the slab lives in registers.  Measured from
+// z0 - 1, a detector column's row crossings rise by E1 < 1 per row, so the
+// unit interval j of heights, [j, j + 1), j = 0 .. ZS, holds floor(1/E1) or
+// ceil(1/E1) rows (K = ceil(1/E1) slots, the later ones predicated).  With
+// S_j the interval's sum of y and T_j its sum of y t (t = the row's height
+// above j), the tent weights give voxel z0 - 1 + j the share hb (S_j - T_j)
+// and voxel z0 + j the share hb T_j -- the slab kernel's two taps per row,
+// summed per interval, every accumulator index fixed at compile time.
+constexpr int BR_TX = 32, BR_TY = 4, BR_THREADS = BR_TX * BR_TY;
+#ifndef MGCT_BR_Z
+#define MGCT_BR_Z 16
+#endif
+// measured at 256^3 / 720 views per grid-0 launch (slab kernel 42.5 ms):
+// 16 voxels, the later slots' rows loaded before their test, 40 registers
+// (12 blocks per SM) 35.1 ms; with 24 voxels 37.9, with 8 voxels 57.1; with
+// the loads behind the test 38.2; without the register cap (118 registers)
+// 55.7
+#ifndef MGCT_BR_UNCOND
+#define MGCT_BR_UNCOND 1
+#endif
+#ifndef MGCT_BR_MINB
+#define MGCT_BR_MINB 12
+#endif
+constexpr int BR_Z = MGCT_BR_Z;                        // voxels per thread along z
+constexpr float BR_E1_LO = 1.0f / 3.0f + 1e-3f;        // eligible grids: BR_E1_LO < E1 < BR_E1_HI
+constexpr float BR_E1_HI = 1.0f - 1e-3f;
+constexpr float BR_K2 = 0.5f + 1e-3f;                  // E1 above this: at most two rows per interval
+
+// One detector column's rows into acc: off is the element offset of the
+// first row (row v, height w in [0, E1) above z0 - 1) in the view's
+// sinogram.  EDGE: rows outside [0, nv) read as zero (not loaded).
+template <int ZS, int K, bool EDGE, typename ST>
+__device__ __forceinline__ void br_column(float (&acc)[ZS], const ST *__restrict__ sv, int off, int nu, float w,
+                                          float E1, float hb, int v, int nv) {
+#pragma unroll
+    for (int j = 0; j <= ZS; ++j) {
+        float y = 0.0f;
+        if (!EDGE || (unsigned)v < (unsigned)nv) y = to_f32(__ldg(sv + off));
+        float S = y, T = y * w;
+        float wn = w + E1;  // height of the next row above j
+        int adv = 1;
+#pragma unroll
+        for (int s = 1; s < K; ++s) {
+            if (MGCT_BR_UNCOND && !EDGE) {
+                // the row after the interval's last lies within the rows the
+                // launch checked, so the load need not wait for the test
+                const float yl = to_f32(__ldg(sv + off + s * nu));
+                const bool in = wn < 1.0f;
+                const float ys = in ? yl : 0.0f;
+                S += ys;
+                T = fmaf(ys, wn, T);
+                if (in) {
+                    wn += E1;
+                    adv = s + 1;
+                }
+            } else if (wn < 1.0f) {
+                float ys = 0.0f;
+                if (!EDGE || (unsigned)(v + s) < (unsigned)nv) ys = to_f32(__ldg(sv + off + s * nu));
+                S += ys;
+                T = fmaf(ys, wn, T);
+                wn += E1;
+                adv = s + 1;
+            }
+        }
+        if (j >= 1) acc[j - 1] = fmaf(hb, S - T, acc[j - 1]);
+        if (j < ZS) acc[j] = fmaf(hb, T, acc[j]);
+        w = wn - 1.0f;  // the first row of interval j + 1
+        off += adv * nu;
+        if (EDGE) v += adv;
+    }
+}
+
+template <typename ST, int ZS>
+__global__ void __launch_bounds__(BR_THREADS, MGCT_BR_MINB)
+    k_backproject_reg(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
+                      float *__restrict__ out, int accumulate) {
+    const int tid = threadIdx.x;
+    const int jx = blockIdx.x * BR_TX + (tid % BR_TX), jy = blockIdx.y * BR_TY + tid / BR_TX;
+    // blockIdx.z = split * (z-slabs) + slab, as in k_backproject_slab
+    const int zblocks = gridDim.z / a.splits;
+    const int split = blockIdx.z / zblocks;
+    const int z0 = (blockIdx.z - split * zblocks) * ZS;
+    const int per = (a.nviews + a.splits - 1) / a.splits;
+    const int i0 = split * per, i1 = min(a.nviews, i0 + per);
+    if (jx >= a.n || jy >= a.n) return;
+    float acc[ZS];
+#pragma unroll
+    for (int q = 0; q < ZS; ++q) acc[q] = 0.0f;
+    const float ic = 0.5f * (float)(a.n - 1);
+    const float cu = 0.5f * (float)(a.nu - 1), cv = 0.5f * (float)(a.nv - 1);
+    const float cx = (float)jx - ic, cy = (float)jy - ic;
+    const float zlo = (float)z0 - 1.0f;  // interval 0 starts here
+    const int nrb_max = (int)((float)(ZS + 1) / BR_E1_LO) + 6;
+    const size_t view_elems = (size_t)a.nu * a.nv;
+    for (int i = i0; i < i1; ++i) {
+        const int k = a.view0 + i * a.stride;
+        const float *G = reinterpret_cast<const float *>(a.views + k);
+        const float X = (float)jx - __ldg(G + 0), Y = (float)jy - __ldg(G + 1);
+        const float Q0 = __ldg(G + 12), Q1 = __ldg(G + 13), Q6 = __ldg(G + 18), Q7 = __ldg(G + 19);
+        const float q2 = fmaf(Q7, Y, Q6 * X);
+        const float u0 = fmaf(Q1, Y, Q0 * X) * __frcp_rn(q2);
+        const float hu = (fabsf(Q0 - u0 * Q6) + fabsf(Q1 - u0 * Q7)) * __frcp_rn(q2 - __ldg(G + 21));
+        const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
+        const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
+        const ST *__restrict__ sv = sino + (size_t)i * view_elems;
+        const float4 *__restrict__ ct = cols + (size_t)k * a.nu * 2;
+        for (int ju = ulo; ju <= uhi; ++ju) {
+            const float4 t0 = __ldg(ct + 2 * ju);
+            const float4 t1 = __ldg(ct + 2 * ju + 1);
+            const bool ay = t0.x != 0.0f;
+            const float ca = ay ? cy : cx, cb = ay ? cx : cy;
+            const float hb = 1.0f - fabsf(fmaf(ca, t0.y, t0.z) - cb);
+            if (hb <= 0.0f) continue;
+            const float E0 = fmaf(ca, t1.x, t0.w) + ic;  // uncentred z crossing at v' = 0
+            const float E1 = fmaf(ca, t1.z, t1.y);
+            // the launch checks the grid's range of E1; this keeps every read
+            // in bounds whatever the table holds
+            if (!(E1 > 0.3f && E1 < 1.0f)) continue;
+            const float rE = __frcp_rn(E1);
+            // first row at or above z0 - 1 (one correction for the rounded quotient)
+            float vf = ceilf(fmaf(zlo - E0, rE, cv));
+            if (!(fabsf(vf) < 1.0e7f)) continue;
+            float w = fmaf(vf - cv, E1, E0) - zlo;
+            if (w < 0.0f) {
+                vf += 1.0f;
+                w += E1;
+            } else if (w >= E1) {
+                vf -= 1.0f;
+                w -= E1;
+            }
+            const int vs = (int)vf;
+            // rows read: those of heights [0, ZS + 1), at most (ZS + 1) / E1 + 1
+            // (the truncation below loses one), one more for the drift of the
+            // stepped heights, two after the last that the unconditional
+            // slots may read, and one spare
+            const int nrb = min(nrb_max, (int)((float)(ZS + 1) * rE) + 6);
+            if (vs >= a.nv || vs + nrb <= 0) continue;
+            const int off = vs * a.nu + ju;
+            if (vs >= 0 && vs + nrb <= a.nv) {
+                if (E1 > BR_K2) br_column<ZS, 2, false>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
+                else br_column<ZS, 3, false>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
+            } else {
+                if (E1 > BR_K2) br_column<ZS, 2, true>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
+                else br_column<ZS, 3, true>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
+            }
+        }
+    }
+    const size_t nvox = (size_t)a.n * a.n * a.n;
+    float *o = out + (size_t)split * nvox;
+#pragma unroll
+    for (int zz = 0; zz < ZS; ++zz) {
+        const int z = z0 + zz;
+        if (z < a.n) {
+            const size_t idx = ((size_t)z * a.n + jy) * a.n + jx;
+            float v = acc[zz];
+            if (accumulate) v += o[idx];
+            o[idx] = v;
+        }
+    }
+}
+
 // Column table (see LevelInfo::d_cols): one thread per (view, column); the
 // axis choice is the projector's own ray_dir() at v' = 0.
 __global__ void k_column_table(const ViewGeom *__restrict__ views, int K, int nu, float4 *__restrict__ cols) {
@@ -525,6 +693,29 @@ int slab_splits(KF kernel, int blocks, int nviews, size_t vol_floats, size_t cap
     return sp < 1 ? 1 : sp;
 }
 
+// The register kernel's launch (see k_backproject_reg), with the slab
+// kernel's view splits.
+template <typename ST>
+int launch_backproject_reg(const LevelInfo &L, BPArgs a, const ST *sino, float *out, int accumulate, cudaStream_t s,
+                           float *split_buf, size_t cap) {
+    dim3 grid((L.n + BR_TX - 1) / BR_TX, (L.n + BR_TY - 1) / BR_TY, (L.n + BR_Z - 1) / BR_Z);
+    const size_t vol_floats = (size_t)L.n * L.n * L.n;
+    if (split_buf && a.nviews > 1)
+        a.splits = slab_splits(k_backproject_reg<ST, BR_Z>, (int)(grid.x * grid.y * grid.z), a.nviews, vol_floats,
+                               cap);
+    if (a.splits == 1) {
+        MGCT_KERNEL(KK_BACKPROJECT, s,
+                    k_backproject_reg<ST, BR_Z><<<grid, BR_THREADS, 0, s>>>(a, L.d_cols, sino, out, accumulate));
+    } else {
+        grid.z *= a.splits;
+        MGCT_KERNEL(KK_BACKPROJECT, s,
+                    k_backproject_reg<ST, BR_Z><<<grid, BR_THREADS, 0, s>>>(a, L.d_cols, sino, split_buf, 0));
+        const int sb = (int)((vol_floats + 255) / 256 < 4096 ? (vol_floats + 255) / 256 : 4096);
+        MGCT_KERNEL(KK_BACKPROJECT, s, k_sum_splits<<<sb, 256, 0, s>>>(vol_floats, a.splits, split_buf, out, accumulate));
+    }
+    return MGCT_OK;
+}
+
 // NCH = 2 writes channel c to out + c * n^3.  WEIGHTED: the sinogram carries
 // each ray's dl already (internal solver path).  split_buf (cap floats, or
 // NULL): scratch for partial volumes, with which an under-filled slab launch
@@ -543,7 +734,10 @@ int launch_backproject(const mgct_geom *g, int level, int view0, int nviews, int
     a.stride = stride;
     a.nviews = nviews;
     a.splits = 1;
-    if (g->separable && WEIGHTED && L.d_cols) {
+    if (MGCT_BS_REG && NCH == 1 && g->separable && WEIGHTED && L.d_cols && L.e1_lo > BR_E1_LO &&
+        L.e1_hi < BR_E1_HI && (size_t)L.nu * (L.nv + 64) < ((size_t)1 << 31)) {
+        if constexpr (NCH == 1) return launch_backproject_reg<ST>(L, a, sino, out, accumulate, s, split_buf, cap);
+    } else if (g->separable && WEIGHTED && L.d_cols) {
         constexpr int Z = SlabCfg<NCH>::Z;
         dim3 grid((L.n + BS_TX - 1) / BS_TX, (L.n + BS_TY - 1) / BS_TY, (L.n + Z - 1) / Z);
         const size_t vol_floats = (size_t)NCH * L.n * L.n * L.n;

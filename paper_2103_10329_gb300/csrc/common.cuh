@@ -62,6 +62,9 @@ struct LevelInfo {
     ViewGeom *d_views;  // device [K]
     float4 *d_cols;     // device [K][nu][2] detector-column table (separable geometries), or NULL
     float4 *d_cols_df;  // device [K][nu][4] the same quantities in double-float, or NULL
+    // range of the column table's z step per detector row, E1 = e10 + c_a e1c,
+    // over every view, column and voxel-centre plane c_a (separable geometries)
+    float e1_lo, e1_hi;
 };
 
 // Detector-column table of a separable geometry (no detector tilt): for view

@@ -6,6 +6,7 @@
 // and source-to-detector distances measured from the source point.  Per-view
 // drift (Sec. 1: thermal drift of the components) shifts source and detector
 // and tilts the detector.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -187,6 +188,45 @@ static int build_view(const mgct_geom *g, int level, int k, ViewGeom *out, std::
     return MGCT_OK;
 }
 
+// Range of E1 = (nv_z + c_a Ev_z) / w_a over every view, column and plane
+// c_a in [-ic, ic] where the column's rays cross the volume (|e_b| <= ic + 1,
+// e_b = c_a rb + pb, the planes at which a voxel column can take them), from
+// the float32 view tables in float64 -- the column table's own quantities.
+// Where |w_x| and |w_y| are within a part in 1e5 of each other both axis
+// choices are counted.
+static void e1_range(LevelInfo &L, const std::vector<ViewGeom> &hv) {
+    double lo = 1e300, hi = -1e300;
+    const double ic = 0.5 * (L.n - 1), cu = 0.5 * (L.nu - 1);
+    for (const ViewGeom &G : hv) {
+        for (int ju = 0; ju < L.nu; ++ju) {
+            const double up = ju - cu;
+            const double wx = (double)G.Wc[0] + up * G.Eu[0], wy = (double)G.Wc[1] + up * G.Eu[1];
+            for (int ax = 0; ax < 2; ++ax) {
+                const double wa = ax ? wy : wx, wb = ax ? wx : wy;
+                if (std::fabs(wa) < std::fabs(wb) * (1.0 - 1e-5)) continue;
+                const float *N = ax ? G.NY : G.NX;
+                const double rb = wb / wa, pb = ((double)N[0] + up * N[1]) / wa;
+                double c0 = -ic, c1 = ic;  // planes where |c_a rb + pb| <= ic + 1
+                if (std::fabs(rb) > 1e-12) {
+                    double e0 = (-ic - 1.0 - pb) / rb, e1 = (ic + 1.0 - pb) / rb;
+                    if (e0 > e1) std::swap(e0, e1);
+                    c0 = std::max(c0, e0);
+                    c1 = std::min(c1, e1);
+                } else if (std::fabs(pb) > ic + 1.0) {
+                    continue;
+                }
+                if (c0 > c1) continue;
+                const double e10 = (double)N[5] / wa, e1c = (double)G.Ev[2] / wa;
+                const double a = e10 + c0 * e1c, b = e10 + c1 * e1c;
+                lo = std::min(lo, std::min(a, b));
+                hi = std::max(hi, std::max(a, b));
+            }
+        }
+    }
+    L.e1_lo = (float)lo;
+    L.e1_hi = (float)hi;
+}
+
 static int upload_tables(mgct_geom *g) {
     int K = g->desc.n_views;
     g->separable = 1;
@@ -209,6 +249,7 @@ static int upload_tables(mgct_geom *g) {
     for (int l = 0; l < g->levels; ++l) {
         LevelInfo &L = g->lev[l];
         if (!g->separable) continue;
+        e1_range(L, g->h_views[l]);
         if (!L.d_cols)
             MGCT_TRY(check_cuda(cudaMalloc(&L.d_cols, (size_t)K * L.nu * 2 * sizeof(float4)), "allocate column table"));
         if (!L.d_cols_df)

@@ -291,10 +291,35 @@ def test_restrict_and_prolong():
         assert np.abs(got - ref).max() <= 1e-6
 
 
+@pytest.mark.parametrize("n,nu,nv,nviews", [(48, 72, 72, 30), (37, 55, 41, 11), (40, 40, 40, 12), (24, 72, 72, 8)],
+                         ids=["rows-finer", "ragged", "rows-coarser", "rows-3x-finer"])
+def test_solver_backprojection_detector_ratios(n, nu, nv, nviews):
+    """The solver's A^T against the oracle at every voxel, for detectors whose
+    rows step the crossing height by 1/3 < E1 < 1 voxel at every plane the
+    rays cross (the register kernel: the first two cases, the second with
+    ragged tiles) and for detectors outside that range (the shared-memory
+    slab kernel): E1 above 1 at the far planes (n = nu) and below 1/3 at the
+    near ones (nu = 3n).  With this scan's pitch the step at the volume
+    centre is about 1.03 n / nu, and it varies by about -35 % / +35 % from
+    the nearest to the farthest plane."""
+    d = scan_desc(n, nu, nv, nviews, 2104, levels=1)
+    g = gpu_geom(d)
+    og = O.level_geometry(oracle_scan(d), 0)
+    y = np.random.default_rng(8).random((nviews, nv, nu)).astype(np.float32)
+    stats = torch.zeros(4, dtype=torch.float64, device="cuda")
+    step = mgct.landweber_direction(g, torch.zeros((n, n, n), device="cuda"), cuda(y), precond=False, stats=stats)
+    alpha = float(stats[0])
+    assert alpha > 0
+    got = to_np(step) / alpha
+    ref = O.backproject(og, y.astype(np.float64))
+    e = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-2 * np.abs(ref).max())
+    check_err(e, TOL_F32)
+
+
 @pytest.mark.parametrize("cfg", [(256, 384, 720), (512, 768, 1440)], ids=["c2", "c3"])
 def test_solver_backprojection_full_size_sampled(cfg):
     """The solver's own A^T (the dl-weighted residual written by the
-    projector's epilogue, then the slab back-projector), in the launch
+    projector's epilogue, then the register back-projector), in the launch
     configuration the bench times: with mu = 0 and no filter the Landweber
     direction is alpha A^T b, so A^T b = step / alpha; sampled voxels
     against the oracle."""

@@ -6,6 +6,8 @@
 // operands and the pipeline are described at k_conv_brick_tc below.
 #pragma once
 
+#include <cuda.h>
+
 #include "conv3d.cuh"
 
 namespace mgct {
@@ -333,6 +335,273 @@ __global__ void __launch_bounds__(128) k_conv_brick_tc(ConvArgs a, int *err) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::NCOLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised form of the haloed-brick implicit GEMM (same tiles, same
+// operand layout, same epilogue as k_conv_brick_tc).
+//
+//   warp 0      producer: one lane loads each unit's brick with the tensor
+//               memory accelerator -- per 8-channel chunk one 5-D box
+//               (8 channels, 10 x, 18 y, 4 z, 1 volume) of a tensor map over
+//               that chunk's channels, zero-filled outside the volume, which
+//               is the convolution's padding -- into a ring of S stages;
+//   warp 1      MMA issuer: one lane issues the unit's tcgen05.mma (27 taps x
+//               TZ planes, K = 16 channels each) once its stage is full,
+//               commits the stage back to the producer and, at a tile's last
+//               unit, the accumulator slot to the epilogue;
+//   warps 2..5  epilogue: read an accumulator slot from tensor memory (warp w
+//               owns lanes 32 (w % 4) ..), add bias, activate, mask, store,
+//               and hand the slot back.
+// Units are 16 channels (CU), so a 110 KB weight set still leaves room for
+// five stages.  Barriers: full[s] (expect-tx by the producer, completed by
+// the copy), empty[s] and accf[slot] (tcgen05.commit), acce[slot] (128
+// epilogue arrivals).  Unit k uses stage k % S, whose (k / S)-th phase it is;
+// tile j uses slot j & 1, its (j >> 1)-th phase.  Every wait is bounded: a
+// role whose wait expires sets the block's flag and *err and stops; before
+// the tensor memory is freed the issuer waits for its last MMAs and the
+// producer for its outstanding copies.
+// ---------------------------------------------------------------------------
+constexpr int WS_THREADS = 192;
+constexpr uint32_t WS_SMEM_MAX = 232448;  // 227 KB per block
+
+struct ConvMaps {
+    CUtensorMap m[8];  // one per 8-channel chunk of the input (Cin <= 64)
+};
+
+template <int CIN, int COUT>
+struct WsCfg {
+    static constexpr int CU = 16;          // channels per unit
+    static constexpr int NU = CIN / CU;    // units per tile
+    static constexpr int CC = CU / 8;      // chunks per unit
+    static constexpr int KC = CIN / 8;     // chunks per weight row
+    static constexpr uint32_t W_BYTES = 27u * COUT * CIN * 2;
+    static constexpr uint32_t BRICK_BYTES = CC * BK_CSTR;
+    static constexpr int S_FIT = (int)((WS_SMEM_MAX - W_BYTES - 1024 - 256) / BRICK_BYTES);
+    static constexpr int S = S_FIT < 6 ? S_FIT : 6;  // stages
+    static constexpr uint32_t SMEM = W_BYTES + S * BRICK_BYTES + 1024;  // + alignment slack
+    static constexpr uint32_t ACC_COLS = BK_TZ * COUT;
+    static constexpr uint32_t NCOLS = 2 * ACC_COLS < 32 ? 32 : 2 * ACC_COLS;
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+// 5-D tiled copy global -> shared (coordinates innermost first), completing
+// `bytes` of the barrier's expected transaction count
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+__global__ void __launch_bounds__(WS_THREADS) k_conv_ws(ConvArgs a, const __grid_constant__ ConvMaps maps, int *err) {
+    static_assert(CIN % 16 == 0 && CIN <= 64 && COUT % 16 == 0 && COUT <= 256, "tcgen05 shape");
+    using C = WsCfg<CIN, COUT>;
+    static_assert(C::S >= 2, "at least two stages");
+    constexpr uint32_t IDESC = tc_idesc_bf16(128, COUT);
+    extern __shared__ unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full[C::S], empty[C::S], accf[2], acce[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int fail;
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+    const uint32_t w_s = smem_u32(base);
+    const uint32_t brick_s = w_s + C::W_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const BrickTiles T = brick_tiles(a.B, a.D, a.H, a.W);
+    const int my_tiles = blockIdx.x < T.ntiles ? (T.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int total = my_tiles * C::NU;
+    volatile int *vfail = &fail;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(C::NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < C::S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&accf[q], 1);
+            mbar_init(&acce[q], 128);
+        }
+        fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // all 27 taps' weights, in the K-major core-matrix layout
+    if (total > 0) {
+        for (int idx = tid; idx < 27 * COUT * C::KC; idx += WS_THREADS) {
+            const int k8 = idx % C::KC, co = (idx / C::KC) % COUT, tap = idx / (C::KC * COUT);
+            cp_async16(w_s + tap * COUT * CIN * 2 + core_off(co, k8, C::KC),
+                       a.w + ((size_t)tap * COUT + co) * CIN + k8 * 8, true);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    auto tile_origin = [&](int j, int &b, int &z0, int &y0, int &x0) {
+        int t = blockIdx.x + j * gridDim.x;
+        x0 = (t % T.ntx) * BK_TX;
+        t /= T.ntx;
+        y0 = (t % T.nty) * BK_TY;
+        t /= T.nty;
+        z0 = (t % T.ntz) * BK_TZ;
+        b = t / T.ntz;
+    };
+    auto give_up = [&]() {
+        *vfail = 1;
+        atomicExch(err, 1);
+    };
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int k = 0; k < total; ++k) {
+                const int s = k % C::S;
+                if (k >= C::S && !mbar_wait_bounded(&empty[s], (uint32_t)((k / C::S - 1) & 1))) {
+                    give_up();
+                    break;
+                }
+                if (*vfail) break;
+                int b, z0, y0, x0;
+                tile_origin(k / C::NU, b, z0, y0, x0);
+                const int ch0 = (k % C::NU) * C::CC;
+                mbar_expect_tx(&full[s], C::BRICK_BYTES);
+#pragma unroll
+                for (int cc = 0; cc < C::CC; ++cc)
+                    tma_load_5d(brick_s + s * C::BRICK_BYTES + cc * BK_CSTR, &maps.m[ch0 + cc], 0, x0 - 1, y0 - 1,
+                                z0 - 1, b, &full[s]);
+                issued = k + 1;
+            }
+            // copies still in flight must land before the block exits
+            for (int k = issued - C::S > 0 ? issued - C::S : 0; k < issued; ++k)
+                mbar_wait_bounded(&full[k % C::S], (uint32_t)((k / C::S) & 1));
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int k = 0; k < total; ++k) {
+                const int s = k % C::S, j = k / C::NU, u = k % C::NU, slot = j & 1;
+                if (u == 0 && j >= 2 && !mbar_wait_bounded(&acce[slot], (uint32_t)(((j >> 1) - 1) & 1))) {
+                    give_up();
+                    break;
+                }
+                if (!mbar_wait_bounded(&full[s], (uint32_t)((k / C::S) & 1))) {
+                    give_up();
+                    break;
+                }
+                if (*vfail) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc0 = tmem + slot * C::ACC_COLS;
+                const uint64_t adesc0 = tc_smem_desc(brick_s + s * C::BRICK_BYTES, BK_CSTR, BK_XB * 16);
+                const uint64_t bdesc0 = tc_smem_desc(w_s + u * C::CC * 128, 128, C::KC * 128);
+#pragma unroll
+                for (int zz = 0; zz < BK_TZ; ++zz) {
+#pragma unroll
+                    for (int tap = 0; tap < 27; ++tap) {
+                        const uint32_t aoff = (((zz + tap / 9) * BK_YB + (tap / 3) % 3) * BK_XB + tap % 3) * 16;
+                        const uint64_t ad = adesc0 + (aoff >> 4);
+                        const uint64_t bd = bdesc0 + ((tap * COUT * CIN * 2) >> 4);
+                        tc_mma(acc0 + zz * COUT, ad, bd, IDESC, (u > 0 || tap > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(&empty[s]);
+                if (u == C::NU - 1) tc_commit(&accf[slot]);
+                issued = k + 1;
+            }
+            // the MMAs issued must end before the tensor memory is freed;
+            // completions arrive in issue order
+            if (issued > 0) mbar_wait_bounded(&empty[(issued - 1) % C::S], (uint32_t)(((issued - 1) / C::S) & 1));
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int ew = warp & 3;  // tensor-memory lane quarter of this warp
+        const bool vec = !OUT_F32 && a.out_ch == COUT && (a.out_stride & 7) == 0;
+        for (int j = 0; j < my_tiles; ++j) {
+            const int slot = j & 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accf[slot], (uint32_t)((j >> 1) & 1)));
+            // warp-uniform: the tensor-memory loads below are warp-collective
+            if (__any_sync(0xffffffffu, !ok || *vfail)) {
+                if (!ok && lane == 0) give_up();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int b, z0, y0, x0;
+            tile_origin(j, b, z0, y0, x0);
+            const int y = y0 + ew * 4 + (lane >> 3), x = x0 + (lane & 7);
+#pragma unroll
+            for (int zz = 0; zz < BK_TZ; ++zz) {
+                const int z = z0 + zz;
+                const bool inside = z < a.D && y < a.H && x < a.W;
+                const size_t p = inside ? (((size_t)b * a.D + z) * a.H + y) * a.W + x : 0;
+#pragma unroll
+                for (int c0 = 0; c0 < (OUT_F32 ? 16 : COUT); c0 += 16) {
+                    float v[16];
+                    tc_ld16(tmem + ((uint32_t)(ew * 32) << 16) + slot * C::ACC_COLS + zz * COUT + c0, v);
+                    if (!inside) continue;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float t = v[i] + (a.bias ? a.bias[c0 + i] : 0.0f);
+                        if (RELU) t = fmaxf(t, 0.0f);
+                        v[i] = t;
+                    }
+                    if (a.mask) {
+                        const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + p * COUT + c0);
+                        uint4 m4[2] = {mp[0], mp[1]};
+                        const __nv_bfloat16 *m = reinterpret_cast<const __nv_bfloat16 *>(m4);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (!(__bfloat162float(m[i]) > 0.0f)) v[i] = 0.0f;
+                    }
+                    if (OUT_F32) {
+                        static_cast<float *>(a.out)[p] = v[0];
+                    } else if (vec) {
+                        uint4 o[2];
+                        __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(o);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                        uint4 *op =
+                            reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out) + p * a.out_stride + c0);
+                        op[0] = o[0];
+                        op[1] = o[1];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (c0 + i < a.out_ch)
+                                static_cast<__nv_bfloat16 *>(a.out)[p * a.out_stride + c0 + i] =
+                                    __float2bfloat16_rn(v[i]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&acce[slot]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::NCOLS) : "memory");
     }

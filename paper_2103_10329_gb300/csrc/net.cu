@@ -171,10 +171,93 @@ __global__ void k_adam(int n, float *__restrict__ w, const float *__restrict__ g
 // ---------------------------------------------------------------------------
 // launch helpers (dispatch over the fixed layer shapes)
 // ---------------------------------------------------------------------------
+#include <cudaTypedefs.h>
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against libcuda), or NULL where the driver does not provide it
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && f)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// One tensor map per 8-channel chunk of a channels-last bf16 activation
+// [B][D][H][W][CIN]: dimensions (8 channels, W, H, D, B), box (8, 10, 18,
+// TZ + 2, 1) -- one chunk plane of a haloed brick -- zero fill outside.
+// False where the encoder is missing or refuses (the caller then launches
+// the cp.async kernel).
+static bool conv_maps(const ConvArgs &a, int cin, ConvMaps *m) {
+    auto enc = tensor_map_encoder();
+    if (!enc || cin > 64 || cin % 8 || reinterpret_cast<uintptr_t>(a.in) % 16) return false;
+    const cuuint64_t e = 2;  // bytes per element
+    const cuuint64_t dims[5] = {8, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D, (cuuint64_t)a.B};
+    const cuuint64_t strides[4] = {cin * e, (cuuint64_t)a.W * cin * e, (cuuint64_t)a.H * a.W * cin * e,
+                                   (cuuint64_t)a.D * a.H * a.W * cin * e};
+    const cuuint32_t box[5] = {8, BK_XB, BK_YB, BK_ZB, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    for (int c = 0; c < cin / 8; ++c) {
+        void *addr = const_cast<__nv_bfloat16 *>(a.in + c * 8);
+        if (enc(&m->m[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, addr, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+#ifndef MGCT_CONV_WS
+#define MGCT_CONV_WS 1
+#endif
+
+// persistent launch of the warp-specialised kernel (k_conv_ws): one block
+// per SM times the blocks that fit; false if it does not apply
+template <int CIN, int COUT, bool RELU, bool OUT_F32>
+static bool conv_fwd_ws(const ConvArgs &a, int *err, cudaStream_t s, int *st) {
+    using C = WsCfg<CIN, COUT>;
+    ConvMaps maps;
+    if (!MGCT_CONV_WS || !conv_maps(a, CIN, &maps)) return false;
+    auto kern = k_conv_ws<CIN, COUT, RELU, OUT_F32>;
+    static int per_sm = 0, nsm = 0;  // per instantiation
+    if (!per_sm) {
+        int dev = 0, occ = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) != cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WS_THREADS, C::SMEM) != cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            return false;
+        }
+        per_sm = std::min(occ, (int)(512 / C::NCOLS));
+    }
+    const int ntiles = brick_tiles(a.B, a.D, a.H, a.W).ntiles;
+    *st = MGCT_OK;
+    if (ntiles == 0) return true;
+    const int grid = std::min(ntiles, nsm * per_sm);
+    *st = [&]() -> int {
+        MGCT_KERNEL(KK_CONV, s, kern<<<grid, WS_THREADS, C::SMEM, s>>>(a, maps, err));
+        return MGCT_OK;
+    }();
+    return true;
+}
+
 // persistent launch of the brick kernel: one block per SM times the blocks
 // that fit (shared memory, and the 512 tensor-memory columns of an SM)
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 static int conv_fwd_t(const ConvArgs &a, int *err, cudaStream_t s) {
+    int st = MGCT_OK;
+    if (conv_fwd_ws<CIN, COUT, RELU, OUT_F32>(a, err, s, &st)) return st;
     using C = BrickCfg<CIN, COUT>;
     auto kern = k_conv_brick_tc<CIN, COUT, RELU, OUT_F32>;
     static int per_sm = 0, nsm = 0;  // per instantiation

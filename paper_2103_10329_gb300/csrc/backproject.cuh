@@ -469,14 +469,19 @@ constexpr int BR_TX = 32, BR_TY = 4, BR_THREADS = BR_TX * BR_TY;
 #endif
 // measured at 256^3 / 720 views per grid-0 launch (slab kernel 42.5 ms):
 // 16 voxels, the later slots' rows loaded before their test, 40 registers
-// (12 blocks per SM) 35.1 ms; with 24 voxels 37.9, with 8 voxels 57.1; with
-// the loads behind the test 38.2; without the register cap (118 registers)
-// 55.7
+// (12 blocks per SM), the exact column range 31.1 ms; with the cube bound's
+// column range 35.1 (each lane's weighted columns start at a different
+// iteration, so a warp runs more of the expensive ones); with 24 voxels
+// 37.9, with 8 voxels 57.1; with the loads behind the test 38.2; without the
+// register cap (118 registers) 55.7 (cube bound for these five)
 #ifndef MGCT_BR_UNCOND
 #define MGCT_BR_UNCOND 1
 #endif
 #ifndef MGCT_BR_MINB
 #define MGCT_BR_MINB 12
+#endif
+#ifndef MGCT_BR_EXACT
+#define MGCT_BR_EXACT 1
 #endif
 constexpr int BR_Z = MGCT_BR_Z;                        // voxels per thread along z
 constexpr float BR_E1_LO = 1.0f / 3.0f + 1e-3f;        // eligible grids: BR_E1_LO < E1 < BR_E1_HI
@@ -554,11 +559,27 @@ __global__ void __launch_bounds__(BR_THREADS, MGCT_BR_MINB)
         const float *G = reinterpret_cast<const float *>(a.views + k);
         const float X = (float)jx - __ldg(G + 0), Y = (float)jy - __ldg(G + 1);
         const float Q0 = __ldg(G + 12), Q1 = __ldg(G + 13), Q6 = __ldg(G + 18), Q7 = __ldg(G + 19);
-        const float q2 = fmaf(Q7, Y, Q6 * X);
-        const float u0 = fmaf(Q1, Y, Q0 * X) * __frcp_rn(q2);
-        const float hu = (fabsf(Q0 - u0 * Q6) + fabsf(Q1 - u0 * Q7)) * __frcp_rn(q2 - __ldg(G + 21));
-        const int ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
-        const int uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
+        const float q0 = fmaf(Q1, Y, Q0 * X), q2 = fmaf(Q7, Y, Q6 * X);
+        int ulo, uhi;
+        if (MGCT_BR_EXACT) {
+            // a column of x-major rays weights this voxel column iff its rays
+            // cross the plane x = jx strictly between y = jy - 1 and jy + 1,
+            // i.e. iff its u lies between the projections of those two
+            // points; likewise (jx -+ 1, jy) for y-major rays.  Both intervals
+            // hold the voxel column's own projection, so their union is the
+            // interval from the least to the greatest of the four.
+            const float ua = (q0 - Q1) * __frcp_rn(q2 - Q7), ub = (q0 + Q1) * __frcp_rn(q2 + Q7);
+            const float uc = (q0 - Q0) * __frcp_rn(q2 - Q6), ud = (q0 + Q0) * __frcp_rn(q2 + Q6);
+            const float umin = fminf(fminf(ua, ub), fminf(uc, ud)), umax = fmaxf(fmaxf(ua, ub), fmaxf(uc, ud));
+            ulo = max(0, (int)ceilf(umin + cu - 1e-3f));
+            uhi = min(a.nu - 1, (int)floorf(umax + cu + 1e-3f));
+        } else {
+            // projected u range of the voxel column (the cube bound)
+            const float u0 = q0 * __frcp_rn(q2);
+            const float hu = (fabsf(Q0 - u0 * Q6) + fabsf(Q1 - u0 * Q7)) * __frcp_rn(q2 - __ldg(G + 21));
+            ulo = max(0, (int)ceilf(u0 - hu + cu - 1e-3f));
+            uhi = min(a.nu - 1, (int)floorf(u0 + hu + cu + 1e-3f));
+        }
         const ST *__restrict__ sv = sino + (size_t)i * view_elems;
         const float4 *__restrict__ ct = cols + (size_t)k * a.nu * 2;
         for (int ju = ulo; ju <= uhi; ++ju) {

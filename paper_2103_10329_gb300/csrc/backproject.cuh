@@ -532,6 +532,45 @@ __device__ __forceinline__ void br_column(float (&acc)[ZS], const ST *__restrict
     }
 }
 
+// Detector column ju of the view whose sinogram is sv into acc, weighted hb:
+// E0 is the uncentred z crossing of its rays at v' = 0 and E1 its step per
+// row, at the voxel column's plane; the slab's intervals start at zlo.
+template <int ZS, typename ST>
+__device__ __forceinline__ void br_add_column(float (&acc)[ZS], const ST *__restrict__ sv, int ju, int nu, int nv,
+                                              float E0, float E1, float hb, float zlo, float cv) {
+    // the launch checks the grid's range of E1; this keeps every read in
+    // bounds whatever the table holds
+    if (!(E1 > 0.3f && E1 < 1.0f)) return;
+    const float rE = __frcp_rn(E1);
+    // first row at or above z0 - 1 (one correction for the rounded quotient)
+    float vf = ceilf(fmaf(zlo - E0, rE, cv));
+    if (!(fabsf(vf) < 1.0e7f)) return;
+    float w = fmaf(vf - cv, E1, E0) - zlo;
+    if (w < 0.0f) {
+        vf += 1.0f;
+        w += E1;
+    } else if (w >= E1) {
+        vf -= 1.0f;
+        w -= E1;
+    }
+    const int vs = (int)vf;
+    // rows read: those of heights [0, ZS + 1), at most (ZS + 1) / E1 + 1 (the
+    // truncation below loses one), one more for the drift of the stepped
+    // heights, two after the last that the unconditional slots may read, and
+    // one spare
+    constexpr int nrb_max = (int)((float)(ZS + 1) / BR_E1_LO) + 6;
+    const int nrb = min(nrb_max, (int)((float)(ZS + 1) * rE) + 6);
+    if (vs >= nv || vs + nrb <= 0) return;
+    const int off = vs * nu + ju;
+    if (vs >= 0 && vs + nrb <= nv) {
+        if (E1 > BR_K2) br_column<ZS, 2, false>(acc, sv, off, nu, w, E1, hb, vs, nv);
+        else br_column<ZS, 3, false>(acc, sv, off, nu, w, E1, hb, vs, nv);
+    } else {
+        if (E1 > BR_K2) br_column<ZS, 2, true>(acc, sv, off, nu, w, E1, hb, vs, nv);
+        else br_column<ZS, 3, true>(acc, sv, off, nu, w, E1, hb, vs, nv);
+    }
+}
+
 template <typename ST, int ZS>
 __global__ void __launch_bounds__(BR_THREADS, MGCT_BR_MINB)
     k_backproject_reg(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
@@ -552,7 +591,6 @@ __global__ void __launch_bounds__(BR_THREADS, MGCT_BR_MINB)
     const float cu = 0.5f * (float)(a.nu - 1), cv = 0.5f * (float)(a.nv - 1);
     const float cx = (float)jx - ic, cy = (float)jy - ic;
     const float zlo = (float)z0 - 1.0f;  // interval 0 starts here
-    const int nrb_max = (int)((float)(ZS + 1) / BR_E1_LO) + 6;
     const size_t view_elems = (size_t)a.nu * a.nv;
     for (int i = i0; i < i1; ++i) {
         const int k = a.view0 + i * a.stride;
@@ -589,38 +627,7 @@ __global__ void __launch_bounds__(BR_THREADS, MGCT_BR_MINB)
             const float ca = ay ? cy : cx, cb = ay ? cx : cy;
             const float hb = 1.0f - fabsf(fmaf(ca, t0.y, t0.z) - cb);
             if (hb <= 0.0f) continue;
-            const float E0 = fmaf(ca, t1.x, t0.w) + ic;  // uncentred z crossing at v' = 0
-            const float E1 = fmaf(ca, t1.z, t1.y);
-            // the launch checks the grid's range of E1; this keeps every read
-            // in bounds whatever the table holds
-            if (!(E1 > 0.3f && E1 < 1.0f)) continue;
-            const float rE = __frcp_rn(E1);
-            // first row at or above z0 - 1 (one correction for the rounded quotient)
-            float vf = ceilf(fmaf(zlo - E0, rE, cv));
-            if (!(fabsf(vf) < 1.0e7f)) continue;
-            float w = fmaf(vf - cv, E1, E0) - zlo;
-            if (w < 0.0f) {
-                vf += 1.0f;
-                w += E1;
-            } else if (w >= E1) {
-                vf -= 1.0f;
-                w -= E1;
-            }
-            const int vs = (int)vf;
-            // rows read: those of heights [0, ZS + 1), at most (ZS + 1) / E1 + 1
-            // (the truncation below loses one), one more for the drift of the
-            // stepped heights, two after the last that the unconditional
-            // slots may read, and one spare
-            const int nrb = min(nrb_max, (int)((float)(ZS + 1) * rE) + 6);
-            if (vs >= a.nv || vs + nrb <= 0) continue;
-            const int off = vs * a.nu + ju;
-            if (vs >= 0 && vs + nrb <= a.nv) {
-                if (E1 > BR_K2) br_column<ZS, 2, false>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
-                else br_column<ZS, 3, false>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
-            } else {
-                if (E1 > BR_K2) br_column<ZS, 2, true>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
-                else br_column<ZS, 3, true>(acc, sv, off, a.nu, w, E1, hb, vs, a.nv);
-            }
+            br_add_column<ZS>(acc, sv, ju, a.nu, a.nv, fmaf(ca, t1.x, t0.w) + ic, fmaf(ca, t1.z, t1.y), hb, zlo, cv);
         }
     }
     const size_t nvox = (size_t)a.n * a.n * a.n;

@@ -366,6 +366,9 @@ __global__ void __launch_bounds__(128) k_conv_brick_tc(ConvArgs a, int *err) {
 // producer for its outstanding copies.
 // ---------------------------------------------------------------------------
 constexpr int WS_THREADS = 192;
+#ifndef MGCT_CONV_TAPOUTER
+#define MGCT_CONV_TAPOUTER 1
+#endif
 constexpr uint32_t WS_SMEM_MAX = 232448;  // 227 KB per block
 
 struct ConvMaps {
@@ -517,14 +520,14 @@ __global__ void __launch_bounds__(WS_THREADS) k_conv_ws(ConvArgs a, const __grid
                 const uint64_t adesc0 = tc_smem_desc(brick_s + s * C::BRICK_BYTES, BK_CSTR, BK_XB * 16);
                 const uint64_t bdesc0 = tc_smem_desc(w_s + u * C::CC * 128, 128, C::KC * 128);
 #pragma unroll
-                for (int zz = 0; zz < BK_TZ; ++zz) {
-#pragma unroll
-                    for (int tap = 0; tap < 27; ++tap) {
-                        const uint32_t aoff = (((zz + tap / 9) * BK_YB + (tap / 3) % 3) * BK_XB + tap % 3) * 16;
-                        const uint64_t ad = adesc0 + (aoff >> 4);
-                        const uint64_t bd = bdesc0 + ((tap * COUT * CIN * 2) >> 4);
-                        tc_mma(acc0 + zz * COUT, ad, bd, IDESC, (u > 0 || tap > 0) ? 1u : 0u);
-                    }
+                for (int o = 0; o < BK_TZ * 27; ++o) {
+                    // MGCT_CONV_TAPOUTER: the planes' accumulators alternate, tap by tap
+                    const int zz = MGCT_CONV_TAPOUTER ? o % BK_TZ : o / 27;
+                    const int tap = MGCT_CONV_TAPOUTER ? o / BK_TZ : o % 27;
+                    const uint32_t aoff = (((zz + tap / 9) * BK_YB + (tap / 3) % 3) * BK_XB + tap % 3) * 16;
+                    const uint64_t ad = adesc0 + (aoff >> 4);
+                    const uint64_t bd = bdesc0 + ((tap * COUT * CIN * 2) >> 4);
+                    tc_mma(acc0 + zz * COUT, ad, bd, IDESC, (u > 0 || tap > 0) ? 1u : 0u);
                 }
                 tc_commit(&empty[s]);
                 if (u == C::NU - 1) tc_commit(&accf[slot]);

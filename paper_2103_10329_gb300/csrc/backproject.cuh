@@ -463,7 +463,21 @@ __global__ void __launch_bounds__(BS_THREADS)
 // above j), the tent weights give voxel z0 - 1 + j the share hb (S_j - T_j)
 // and voxel z0 + j the share hb T_j -- the slab kernel's two taps per row,
 // summed per interval, every accumulator index fixed at compile time.
-constexpr int BR_TX = 32, BR_TY = 4, BR_THREADS = BR_TX * BR_TY;
+#ifndef MGCT_BR_BX
+#define MGCT_BR_BX 32
+#endif
+#ifndef MGCT_BR_WX
+#define MGCT_BR_WX 8
+#endif
+// a block is BR_TX x BR_TY voxel columns; a warp BR_WX x (32 / BR_WX) of them.
+// Measured per grid-0 launch at 256^3 / 720 views (512^3 / 1440): warps of
+// 32 x 1 columns 31.2 ms (452), 16 x 2 30.2 (442), 8 x 4 29.5 (435), and
+// 4 x 8 or 8 x 4 in 16 x 8 and 8 x 16 blocks 29.4-29.8 (433-439): on views
+// whose rays run along a warp's long side, its lanes' detector columns and
+// rows spread apart
+constexpr int BR_TX = MGCT_BR_BX, BR_TY = 128 / BR_TX, BR_THREADS = BR_TX * BR_TY;
+constexpr int BR_WX = MGCT_BR_WX, BR_WY = 32 / BR_WX;
+static_assert(BR_TX % BR_WX == 0 && BR_TY % BR_WY == 0, "warp tiles must tile the block");
 #ifndef MGCT_BR_Z
 #define MGCT_BR_Z 16
 #endif
@@ -576,7 +590,9 @@ __global__ void __launch_bounds__(BR_THREADS, MGCT_BR_MINB)
     k_backproject_reg(BPArgs a, const float4 *__restrict__ cols, const ST *__restrict__ sino,
                       float *__restrict__ out, int accumulate) {
     const int tid = threadIdx.x;
-    const int jx = blockIdx.x * BR_TX + (tid % BR_TX), jy = blockIdx.y * BR_TY + tid / BR_TX;
+    const int w = tid >> 5, l = tid & 31;
+    const int jx = blockIdx.x * BR_TX + (w % (BR_TX / BR_WX)) * BR_WX + l % BR_WX;
+    const int jy = blockIdx.y * BR_TY + (w / (BR_TX / BR_WX)) * BR_WY + l / BR_WX;
     // blockIdx.z = split * (z-slabs) + slab, as in k_backproject_slab
     const int zblocks = gridDim.z / a.splits;
     const int split = blockIdx.z / zblocks;
